@@ -1,0 +1,183 @@
+/*
+ * daq.h - C ABI of the GB300 (sm_103a) muon g-2 waveform DAQ hot path.
+ *
+ * The library runs, on one GPU, the per-fill processing of 12-bit, 800 MSPS
+ * calorimeter waveforms that W. Gohn, "Data Acquisition with GPUs: The DAQ
+ * for the Muon g-2 Experiment at Fermilab" (arXiv:1611.04959), Sec. 3 and
+ * Table 2, assigns to the GPU:
+ *   T-method: sum the crystals of a calorimeter sample by sample, subtract
+ *             pedestals, apply a threshold, add pre- and post-samples, merge
+ *             overlapping windows into islands, save every crystal's raw
+ *             samples over each island (Table 2 rows 1-6; Sec. 3 T-method);
+ *   Q-method: decimate the pedestal-subtracted sum and accumulate it fill by
+ *             fill into histograms (Table 2 rows 7-8; Sec. 3 Q-method).
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked "device" are CUDA device (or managed) addresses on the
+ *     current device; "host" pointers are ordinary host memory.
+ *   - The caller owns every buffer.  daq_process_fills allocates nothing; it
+ *     enqueues work on params->stream and returns without waiting, unless
+ *     DAQ_SYNC is set.
+ *   - Return values are daq_status codes (0 = success, negative = error).
+ *     Nothing in the library aborts, traps or exits the process.
+ */
+#ifndef DAQ_H
+#define DAQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum daq_status {
+    DAQ_OK = 0,
+    DAQ_EINVAL = -1,       /* bad shape, parameter, null or misaligned pointer, short workspace */
+    DAQ_ECAPACITY = -2,    /* island records or pool rows did not fit; counts hold the sizes needed */
+    DAQ_ECUDA = -3,        /* a CUDA call or kernel launch failed */
+    DAQ_ETIMEOUT = -4,     /* a bounded device-side wait gave up; outputs are incomplete */
+    DAQ_EUNSUPPORTED = -5  /* valid request this build does not handle (e.g. n_xtal > 64) */
+};
+
+/* params->flags */
+#define DAQ_SKIP_Q 1u        /* leave qhist_inout untouched */
+#define DAQ_SKIP_ISLANDS 2u  /* compute counts, write no island records, pool rows or pedestals */
+#define DAQ_SYNC 4u          /* wait for the stream, then return the device-side status */
+
+/* Bits of counts[2] (device-side status, OR-ed by the kernels). */
+#define DAQ_DEV_HDR_OVERFLOW 1
+#define DAQ_DEV_POOL_OVERFLOW 2
+#define DAQ_DEV_TIMEOUT 4
+#define DAQ_DEV_BAD_FILL_LEN 8
+
+/*
+ * One island (Table 2 row 5 "save an array of identified islands"; Sec. 3:
+ * the array of island data goes back to host memory).  An island is a maximal
+ * run of samples [start, start + len) of one calorimeter-fill whose
+ * pedestal-subtracted crystal sum crosses the threshold somewhere within
+ * [t - post, t + pre] of each sample t.  Its raw samples are pool rows
+ * pool_row .. pool_row + len - 1.  24 bytes, naturally aligned.
+ */
+typedef struct daq_island {
+    int32_t fill;     /* params->fill_base + fill index within the call */
+    int32_t calo;     /* calorimeter index */
+    int32_t start;    /* first sample of the island */
+    int32_t len;      /* number of samples */
+    int64_t pool_row; /* first pool row holding the island's samples */
+} daq_island;
+
+/*
+ * Parameters of one call.  Initialise with daq_params_default().
+ *   threshold    T: a sample crosses when S[t] > T, S = crystal sum minus the
+ *                summed pedestals (Table 2 row 2; Sec. 3 T-method).
+ *   pre, post    samples added before / after every crossing (Table 2 row 3);
+ *                0 <= pre, post; pre + post <= 512.
+ *   ped_samples  pedestal window: the first ped_samples samples of each crystal
+ *                (Table 2 row 1 uses 100); >= 1.  Each crystal's pedestal is
+ *                floor((sum + floor(n/2)) / n), n = min(ped_samples, fill length).
+ *   n_decim      number of Q decimation factors (0, 1 or 2); decim[i] >= 1.
+ *   fill_base    added to the fill index written into island records.
+ *   fill_len     device int32[n_fills] fill lengths (0 <= len <= n_samples), or
+ *                NULL for n_samples each.  Out-of-range values are clamped and
+ *                flagged with DAQ_DEV_BAD_FILL_LEN.
+ *   flags        DAQ_SKIP_Q | DAQ_SKIP_ISLANDS | DAQ_SYNC.
+ *   tile         samples per tile: 0 = default (448); else 128, 224, 448 or 960.
+ *   grid         CTAs: 0 = persistent (resident CTAs per SM x SMs);
+ *                -1 = one CTA per tile (the plain, non-persistent form);
+ *                > 0 = exactly this many persistent CTAs.
+ *   stream       cudaStream_t (NULL = legacy default stream).
+ *   workspace    device scratch of at least daq_workspace_size() bytes,
+ *                16-byte aligned; reused by the call and not to be shared by
+ *                calls that may run at the same time.
+ */
+typedef struct daq_params {
+    int32_t threshold;
+    int32_t pre;
+    int32_t post;
+    int32_t ped_samples;
+    int32_t n_decim;
+    int32_t decim[2];
+    int32_t fill_base;
+    const int32_t *fill_len;
+    uint32_t flags;
+    int32_t tile;
+    int32_t grid;
+    int32_t reserved;
+    void *stream;
+    void *workspace;
+    size_t workspace_bytes;
+} daq_params;
+
+/*
+ * Outputs (all device pointers, caller-owned).
+ *   hdr, hdr_cap        island records, in (fill, calo, start) order.
+ *   pool, pool_row_cap  pool rows, time-major: row r holds the n_xtal raw int16
+ *                       samples of the r-th marked sample (row stride n_xtal
+ *                       int16); 16-byte aligned.
+ *   pedestal            int32[n_fills][n_calo][n_xtal] per-crystal pedestals, or NULL.
+ *   counts              int64[4]: [0] islands found, [1] pool rows found (both
+ *                       the full sizes, even when capacity ran out), [2] device
+ *                       status bits DAQ_DEV_*, [3] tiles processed.  Readable
+ *                       once the stream has reached the end of the call.
+ * Records and rows beyond their capacity are not written (DAQ_DEV_*_OVERFLOW).
+ */
+typedef struct daq_islands {
+    daq_island *hdr;
+    int64_t hdr_cap;
+    int16_t *pool;
+    int64_t pool_row_cap;
+    int32_t *pedestal;
+    int64_t *counts;
+} daq_islands;
+
+/* Fill *p with the defaults: T = 30, pre = 8, post = 24, ped_samples = 100,
+ * one decimation factor 32, everything else zero / NULL. */
+void daq_params_default(daq_params *p);
+
+/*
+ * Bytes of device workspace daq_process_fills needs for these sizes and
+ * parameters (tile choice, fills).  Returns DAQ_OK or DAQ_EINVAL.
+ */
+int daq_workspace_size(int n_calo, int n_xtal, int64_t n_samples, int n_fills, const daq_params *params,
+                       size_t *bytes);
+
+/*
+ * Bins per calorimeter of the Q histogram for decimation factor D:
+ * ceil(n_samples / D).  qhist_inout holds n_calo x bins(decim[0]) int64 values,
+ * followed (if n_decim == 2) by n_calo x bins(decim[1]).
+ */
+int64_t daq_q_bins(int64_t n_samples, int32_t decim);
+
+/*
+ * Process n_fills fills of n_calo calorimeters in one launch sequence.
+ *   samples      device int16[n_fills][n_calo][n_xtal][n_samples] (row pitch
+ *                n_samples; 12-bit ADC values in 16-bit words, Sec. 3); the
+ *                fast path wants 16-byte aligned rows (n_samples % 8 == 0).
+ *   n_xtal       crystals per calorimeter, 1..64 (the experiment has 54, Sec. 3).
+ *   qhist_inout  device int64 Q histograms (layout: see daq_q_bins); B_D[k] =
+ *                sum of S over samples [kD, min(kD + D, len)) is ADDED to bin k
+ *                of the fill's calorimeter for every fill (Table 2 rows 7-8).
+ * Every output is an integer, so results are bit-exact and independent of
+ * tile size, grid and scheduling.  Returns DAQ_OK once enqueued; with
+ * DAQ_SYNC it waits and returns DAQ_ECAPACITY / DAQ_ETIMEOUT / DAQ_EINVAL
+ * from counts[2].
+ */
+int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_samples, int n_fills,
+                      const daq_params *params, const daq_islands *islands_out, int64_t *qhist_inout);
+
+/* Map a host copy of counts[4] to a daq_status (DAQ_OK if no bit is set). */
+int daq_status_from_counts(const int64_t *counts_host);
+
+/* Static, human-readable text for a daq_status. */
+const char *daq_strerror(int status);
+
+/* ABI version (major * 100 + minor). */
+int daq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DAQ_H */

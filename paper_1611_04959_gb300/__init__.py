@@ -1,0 +1,200 @@
+"""GB300 (sm_103a) muon g-2 waveform DAQ hot path: Python binding of libdaq.
+
+The binding marshals arguments into the C ABI of include/daq.h (ctypes) and
+uses PyTorch only for device memory and streams.  Every step of the path runs
+in the CUDA kernels of libdaq.so; there is no CPU fallback, and importing the
+binding without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+# status codes and flags (include/daq.h)
+DAQ_OK, DAQ_EINVAL, DAQ_ECAPACITY, DAQ_ECUDA, DAQ_ETIMEOUT, DAQ_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+DAQ_SKIP_Q, DAQ_SKIP_ISLANDS, DAQ_SYNC = 1, 2, 4
+DAQ_DEV_HDR_OVERFLOW, DAQ_DEV_POOL_OVERFLOW, DAQ_DEV_TIMEOUT, DAQ_DEV_BAD_FILL_LEN = 1, 2, 4, 8
+
+ISLAND_DTYPE = np.dtype([("fill", "<i4"), ("calo", "<i4"), ("start", "<i4"), ("len", "<i4"),
+                         ("pool_row", "<i8")])
+
+
+class DaqParams(ctypes.Structure):
+    _fields_ = [("threshold", ctypes.c_int32), ("pre", ctypes.c_int32), ("post", ctypes.c_int32),
+                ("ped_samples", ctypes.c_int32), ("n_decim", ctypes.c_int32), ("decim", ctypes.c_int32 * 2),
+                ("fill_base", ctypes.c_int32), ("fill_len", ctypes.c_void_p), ("flags", ctypes.c_uint32),
+                ("tile", ctypes.c_int32), ("grid", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+class DaqIslands(ctypes.Structure):
+    _fields_ = [("hdr", ctypes.c_void_p), ("hdr_cap", ctypes.c_int64), ("pool", ctypes.c_void_p),
+                ("pool_row_cap", ctypes.c_int64), ("pedestal", ctypes.c_void_p), ("counts", ctypes.c_void_p)]
+
+
+class DaqError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} ({status})" if what else f"{strerror(status)} ({status})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded libdaq.so.  Raises if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libdaq.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+            L.daq_params_default.argtypes = [ctypes.POINTER(DaqParams)]
+            L.daq_params_default.restype = None
+            L.daq_workspace_size.argtypes = [i32, i32, i64, i32, ctypes.POINTER(DaqParams),
+                                             ctypes.POINTER(ctypes.c_size_t)]
+            L.daq_workspace_size.restype = i32
+            L.daq_q_bins.argtypes = [i64, ctypes.c_int32]
+            L.daq_q_bins.restype = i64
+            L.daq_process_fills.argtypes = [vp, i32, i32, i64, i32, ctypes.POINTER(DaqParams),
+                                            ctypes.POINTER(DaqIslands), vp]
+            L.daq_process_fills.restype = i32
+            L.daq_status_from_counts.argtypes = [vp]
+            L.daq_status_from_counts.restype = i32
+            L.daq_strerror.argtypes = [i32]
+            L.daq_strerror.restype = ctypes.c_char_p
+            L.daq_version.argtypes = []
+            L.daq_version.restype = i32
+            _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().daq_strerror(int(status)).decode()
+
+
+# ------------------------------------------------------------------- same names as the C ABI
+def daq_params_default() -> DaqParams:
+    p = DaqParams()
+    lib().daq_params_default(ctypes.byref(p))
+    return p
+
+
+def daq_workspace_size(n_calo: int, n_xtal: int, n_samples: int, n_fills: int, params: DaqParams) -> int:
+    out = ctypes.c_size_t(0)
+    rc = lib().daq_workspace_size(n_calo, n_xtal, n_samples, n_fills, ctypes.byref(params), ctypes.byref(out))
+    if rc:
+        raise DaqError(rc, "daq_workspace_size")
+    return int(out.value)
+
+
+def daq_q_bins(n_samples: int, decim: int) -> int:
+    return int(lib().daq_q_bins(n_samples, decim))
+
+
+def daq_process_fills(samples_ptr: int, n_calo: int, n_xtal: int, n_samples: int, n_fills: int,
+                      params: DaqParams, islands: DaqIslands, qhist_ptr: int | None) -> int:
+    return int(lib().daq_process_fills(samples_ptr, n_calo, n_xtal, n_samples, n_fills, ctypes.byref(params),
+                                       ctypes.byref(islands), qhist_ptr))
+
+
+def daq_status_from_counts(counts_host) -> int:
+    c = np.ascontiguousarray(counts_host, dtype=np.int64)
+    return int(lib().daq_status_from_counts(c.ctypes.data))
+
+
+# ------------------------------------------------------------------- torch marshalling helpers
+def make_params(threshold=30, pre=8, post=24, ped_samples=100, decim=(32,), fill_base=0, fill_len=None,
+                flags=0, tile=0, grid=0, stream=None, workspace=None) -> DaqParams:
+    p = daq_params_default()
+    p.threshold, p.pre, p.post, p.ped_samples = int(threshold), int(pre), int(post), int(ped_samples)
+    decim = tuple(decim)
+    p.n_decim = len(decim)
+    for i, d in enumerate(decim):
+        p.decim[i] = int(d)
+    p.fill_base = int(fill_base)
+    p.fill_len = None if fill_len is None else int(fill_len.data_ptr())
+    p.flags = int(flags)
+    p.tile, p.grid = int(tile), int(grid)
+    p.stream = None if stream is None else int(stream.cuda_stream)
+    if workspace is not None:
+        p.workspace = int(workspace.data_ptr())
+        p.workspace_bytes = int(workspace.numel() * workspace.element_size())
+    return p
+
+
+def q_size(n_calo: int, n_samples: int, decim) -> int:
+    return sum(n_calo * daq_q_bins(n_samples, d) for d in decim)
+
+
+class Outputs:
+    """Caller-owned device buffers of one call (torch tensors)."""
+
+    def __init__(self, torch, device, n_fills, n_calo, n_xtal, hdr_cap, pool_cap, pedestal=True):
+        self.hdr = torch.empty(max(1, hdr_cap) * 3, dtype=torch.int64, device=device)
+        self.hdr_cap = int(hdr_cap)
+        self.pool = torch.empty((max(1, pool_cap), n_xtal), dtype=torch.int16, device=device)
+        self.pool_cap = int(pool_cap)
+        self.pedestal = (torch.empty((n_fills, n_calo, n_xtal), dtype=torch.int32, device=device)
+                         if pedestal else None)
+        self.counts = torch.zeros(4, dtype=torch.int64, device=device)
+
+    def struct(self) -> DaqIslands:
+        return DaqIslands(self.hdr.data_ptr(), self.hdr_cap, self.pool.data_ptr(), self.pool_cap,
+                          None if self.pedestal is None else self.pedestal.data_ptr(), self.counts.data_ptr())
+
+    def islands_host(self, n: int) -> np.ndarray:
+        n = min(int(n), self.hdr_cap)
+        raw = self.hdr[: n * 3].cpu().numpy()
+        return raw.view(ISLAND_DTYPE)[:n].copy()
+
+
+def process_fills(samples, threshold=30, pre=8, post=24, ped_samples=100, decim=(32,), fill_len=None,
+                  fill_base=0, q=None, outputs: Outputs | None = None, hdr_cap=None, pool_cap=None,
+                  workspace=None, flags=0, tile=0, grid=0, stream=None, sync=True) -> dict:
+    """Run the path on a CUDA int16 tensor samples[F][C][X][N].
+
+    Allocates (with torch) whatever output the caller did not pass; returns a
+    dict with the tensors, the host counts (when sync) and the status."""
+    import torch
+    if not samples.is_cuda or samples.dtype != torch.int16 or samples.dim() != 4 or not samples.is_contiguous():
+        raise ValueError("samples must be a contiguous CUDA int16 tensor [fills][calo][xtal][samples]")
+    F, C, X, N = (int(v) for v in samples.shape)
+    dev = samples.device
+    decim = tuple(decim)
+    if fill_len is not None and not torch.is_tensor(fill_len):
+        fill_len = torch.as_tensor(np.asarray(fill_len, np.int32), device=dev)
+    if outputs is None:
+        rows = F * C * N if fill_len is None else C * int(fill_len.clamp(0, N).sum().item())
+        hdr_cap = rows // 2 + F * C + 1 if hdr_cap is None else hdr_cap
+        pool_cap = rows if pool_cap is None else pool_cap
+        outputs = Outputs(torch, dev, F, C, X, hdr_cap, pool_cap)
+    if q is None and decim:
+        q = torch.zeros(q_size(C, N, decim), dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev) if stream is None else stream
+    p = make_params(threshold, pre, post, ped_samples, decim, fill_base, fill_len, flags, tile, grid, stream)
+    ws_bytes = daq_workspace_size(C, X, N, F, p)
+    if workspace is None or workspace.numel() * workspace.element_size() < ws_bytes:
+        workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    p.workspace, p.workspace_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    if sync:
+        p.flags |= DAQ_SYNC
+    rc = daq_process_fills(samples.data_ptr(), C, X, N, F, p, outputs.struct(),
+                           None if q is None else q.data_ptr())
+    res = dict(outputs=outputs, q=q, workspace=workspace, status=rc)
+    if rc not in (DAQ_OK, DAQ_ECAPACITY):
+        raise DaqError(rc, "daq_process_fills")
+    if sync:
+        counts = outputs.counts.cpu().numpy()
+        res.update(counts=counts, n_islands=int(counts[0]), n_rows=int(counts[1]))
+    return res

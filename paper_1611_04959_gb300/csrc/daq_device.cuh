@@ -1,0 +1,194 @@
+// Device-side building blocks for the sm_103a DAQ kernels: inline PTX for
+// mbarrier / bulk async copies, ldmatrix transposes, scoped loads and stores
+// for the cross-CTA scan, and the bounded waits every spin loop uses.
+#pragma once
+
+#include <cstdint>
+
+namespace daq {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---------------------------------------------------------------- mbarrier + bulk copies
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier to complete, giving up after limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 15u) == 15u && global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// Order this thread's earlier generic-proxy accesses to shared memory before
+// later async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bulk global -> shared copy; completion counted in bytes on `bar`.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------- ldmatrix (16-bit transpose)
+// Four 8x8 b16 matrices; lane L gives the address of row L%8 of matrix L/8.
+// With .trans, lane L receives, for each matrix, rows 2(L%4) (low half) and
+// 2(L%4)+1 (high half) of column L/4.
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
+                                              uint32_t &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+// ---------------------------------------------------------------- scoped global accesses
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Streaming 16-byte store (output is written once and not re-read here).
+__device__ __forceinline__ void st_global_cs_v4(void *p, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
+{
+    asm volatile("st.global.cs.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------- warp bit arrays
+// A warp holds a bit array as 32 words, lane k holding bits [32k, 32k + 32).
+// shl_bits moves every bit s places towards higher indices (zeros enter at 0);
+// shr_bits moves them s places towards lower indices (zeros enter at the top).
+__device__ __forceinline__ uint32_t shl_bits(uint32_t v, int s, int lane)
+{
+    const int q = s >> 5, r = s & 31;
+    uint32_t a = q < 32 ? __shfl_up_sync(kFull, v, q & 31) : 0u;
+    uint32_t b = q + 1 < 32 ? __shfl_up_sync(kFull, v, (q + 1) & 31) : 0u;
+    if (lane < q) a = 0u;
+    if (lane < q + 1) b = 0u;
+    return r ? ((a << r) | (b >> (32 - r))) : a;
+}
+
+__device__ __forceinline__ uint32_t shr_bits(uint32_t v, int s, int lane)
+{
+    const int q = s >> 5, r = s & 31;
+    uint32_t a = q < 32 ? __shfl_down_sync(kFull, v, q & 31) : 0u;
+    uint32_t b = q + 1 < 32 ? __shfl_down_sync(kFull, v, (q + 1) & 31) : 0u;
+    if (lane + q > 31) a = 0u;
+    if (lane + q + 1 > 31) b = 0u;
+    return r ? ((a >> r) | (b << (32 - r))) : a;
+}
+
+// Bits [lo, hi) of the 32-bit word that holds array bits [base, base + 32).
+__device__ __forceinline__ uint32_t range_mask(long long base, long long lo, long long hi)
+{
+    long long a = lo - base, b = hi - base;
+    if (a < 0) a = 0;
+    if (b > 32) b = 32;
+    if (b <= a) return 0u;
+    const uint32_t upto_b = b >= 32 ? 0xffffffffu : ((1u << b) - 1u);
+    const uint32_t below_a = a >= 32 ? 0xffffffffu : ((1u << a) - 1u);
+    return upto_b & ~below_a;
+}
+
+template <typename T> __device__ __forceinline__ T warp_excl_scan_add(T v, int lane, T &total)
+{
+    T x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T y = __shfl_up_sync(kFull, x, d);
+        if (lane >= d) x += y;
+    }
+    total = __shfl_sync(kFull, x, 31);
+    return x - v;
+}
+
+__device__ __forceinline__ int warp_excl_scan_max(int v, int lane, int identity)
+{
+    int x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int y = __shfl_up_sync(kFull, x, d);
+        if (lane >= d) x = max(x, y);
+    }
+    int e = __shfl_up_sync(kFull, x, 1);
+    return lane == 0 ? identity : e;
+}
+
+__device__ __forceinline__ int warp_max(int v)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v = max(v, __shfl_xor_sync(kFull, v, d));
+    return v;
+}
+
+}  // namespace daq

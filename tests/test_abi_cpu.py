@@ -1,0 +1,105 @@
+"""The C ABI library loads and exports every declared symbol; host-only calls
+and argument validation work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def daq():
+    from paper_1611_04959_gb300 import build
+    build.build()
+    import paper_1611_04959_gb300 as d
+    return d
+
+
+def declared_functions() -> list:
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(daq_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(daq):
+    names = declared_functions()
+    assert "daq_process_fills" in names and "daq_workspace_size" in names
+    lib = ctypes.CDLL(daq.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_struct_layouts_match_header(daq):
+    # daq_params: 8 int32, pointer, uint32 + 3 int32, 2 pointers, size_t
+    assert ctypes.sizeof(daq.DaqParams) == 32 + 8 + 16 + 8 + 8 + 8
+    assert ctypes.sizeof(daq.DaqIslands) == 6 * 8
+    assert daq.ISLAND_DTYPE.itemsize == 24
+
+
+def test_host_calls(daq):
+    p = daq.daq_params_default()
+    assert (p.threshold, p.pre, p.post, p.ped_samples, p.n_decim, p.decim[0]) == (30, 8, 24, 100, 1, 32)
+    assert daq.daq_q_bins(560_000, 32) == 17_500 and daq.daq_q_bins(560_001, 32) == 17_501
+    ws = daq.daq_workspace_size(24, 54, 560_000, 1, p)
+    tiles = 24 * -(-560_000 // 448)
+    assert ws >= 32 * tiles
+    assert daq.strerror(daq.DAQ_ECAPACITY).startswith("island records")
+    assert daq.lib().daq_version() >= 100
+    assert daq.daq_status_from_counts([5, 5, 0, 1]) == daq.DAQ_OK
+    assert daq.daq_status_from_counts([5, 5, daq.DAQ_DEV_POOL_OVERFLOW, 1]) == daq.DAQ_ECAPACITY
+    assert daq.daq_status_from_counts([5, 5, daq.DAQ_DEV_TIMEOUT, 1]) == daq.DAQ_ETIMEOUT
+
+
+@pytest.mark.parametrize("bad", [
+    dict(pre=-1), dict(post=-2), dict(ped_samples=0), dict(decim=(0,)), dict(pre=300, post=300),
+    dict(tile=100), dict(tile=960, pre=40, post=40),
+])
+def test_bad_parameters_rejected_before_any_device_work(daq, bad):
+    kw = dict(threshold=30, pre=8, post=24, ped_samples=100, decim=(32,))
+    kw.update(bad)
+    p = daq.make_params(**kw)
+    with pytest.raises(daq.DaqError) as e:
+        daq.daq_workspace_size(1, 54, 1000, 1, p)
+    assert e.value.status == daq.DAQ_EINVAL
+
+
+def _has_gpu() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+@pytest.mark.skipif(_has_gpu(), reason="passes fake device addresses; host-only check")
+def test_bad_shapes_rejected(daq):
+    p = daq.make_params()
+    isl = daq.DaqIslands(0, 0, 0, 0, 0, 0)
+    assert daq.daq_process_fills(0, 1, 54, 1000, 1, p, isl, None) == daq.DAQ_EINVAL   # counts NULL
+    assert daq.daq_process_fills(0, 1, 65, 1000, 1, p, isl, None) == daq.DAQ_EUNSUPPORTED
+    assert daq.daq_process_fills(0, 1, 0, 1000, 1, p, isl, None) == daq.DAQ_EINVAL
+    assert daq.daq_process_fills(0, -1, 54, 1000, 1, p, isl, None) == daq.DAQ_EINVAL
+    isl = daq.DaqIslands(0, 0, 0, 0, 0, 64)
+    assert daq.daq_process_fills(0, 1, 54, 1000, 1, p, isl, None) == daq.DAQ_EINVAL   # samples NULL
+    # misaligned pool / short workspace
+    isl = daq.DaqIslands(4096, 10, 4098, 10, 0, 64)
+    assert daq.daq_process_fills(4096, 1, 54, 1000, 1, p, isl, 8192) == daq.DAQ_EINVAL
+    isl = daq.DaqIslands(4096, 10, 4096, 10, 0, 64)
+    p.workspace, p.workspace_bytes = 4096, 16
+    assert daq.daq_process_fills(4096, 1, 54, 1000, 1, p, isl, 8192) == daq.DAQ_EINVAL
+
+
+def test_no_cpu_fallback_when_library_missing(tmp_path, monkeypatch):
+    import paper_1611_04959_gb300 as d
+    monkeypatch.setattr(d, "_lib", None)
+    monkeypatch.setattr(d, "LIB_PATH", str(tmp_path / "libdaq.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        d.lib()

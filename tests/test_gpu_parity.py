@@ -1,0 +1,183 @@
+"""CUDA path vs oracle, bit-exact (every output is an integer).
+
+Each case runs libdaq through the C ABI on seeded synthetic input and compares
+island records, pool rows, pedestals, counts and int64 Q histograms element by
+element with the oracle on the same input."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import synth
+    import paper_1611_04959_gb300 as daq
+    return dict(torch=torch, oracle=oracle, synth=synth, daq=daq)
+
+
+def compare(env, s, params, fill_len=None, n_threads=8, **kw):
+    torch, oracle, daq = env["torch"], env["oracle"], env["daq"]
+    ref = oracle.process_fills(s, params, fill_len=fill_len, n_threads=n_threads)
+    fl = None if fill_len is None else torch.as_tensor(np.asarray(fill_len, np.int32), device="cuda")
+    res = daq.process_fills(torch.from_numpy(s).cuda(), fill_len=fl, **params, **kw)
+    out = res["outputs"]
+    ctx = dict(shape=s.shape, params=params, kw=kw)
+    assert res["status"] == daq.DAQ_OK, (res["status"], res["counts"], ctx)
+    assert res["n_islands"] == ref["n_islands"], ctx
+    assert res["n_rows"] == ref["n_rows"], ctx
+    got_isl = out.islands_host(res["n_islands"])
+    assert np.array_equal(got_isl, ref["islands"]), ctx
+    assert np.array_equal(out.pool[: res["n_rows"]].cpu().numpy(), ref["pool"]), ctx
+    assert np.array_equal(out.pedestal.cpu().numpy(), ref["pedestal"]), ctx
+    if params.get("decim"):
+        assert np.array_equal(res["q"].cpu().numpy(), ref["q"]), ctx
+    return res, ref
+
+
+def test_plain_one_calorimeter_full_fill(env):
+    from synth import workloads as W
+    w = W.PLAIN_1CALO
+    s = env["synth"].generate(w.config())
+    res, ref = compare(env, s, w.params())
+    assert ref["n_islands"] > 100
+
+
+@pytest.mark.parametrize("tile", [128, 224, 448, 960])
+@pytest.mark.parametrize("grid", [0, -1, 1, 5])
+def test_tile_and_grid_invariance(env, tile, grid):
+    from synth import workloads as W
+    w = W.scaled(W.PLAIN_FULL_FILL, n_calo=3, n_samples=40_000)
+    s = env["synth"].generate(w.config())
+    compare(env, s, w.params(), tile=tile, grid=grid)
+
+
+def _random_case(rng):
+    X = int(rng.choice([1, 2, 3, 5, 8, 17, 31, 32, 33, 54, 63, 64]))
+    N = int(rng.integers(1, 6000))
+    if rng.random() < 0.5:
+        N = (N + 7) // 8 * 8
+    F, C = int(rng.integers(1, 4)), int(rng.integers(1, 4))
+    pre, post = int(rng.integers(0, 40)), int(rng.integers(0, 70))
+    if rng.random() < 0.2:
+        pre, post = int(rng.integers(0, 250)), int(rng.integers(0, 250))
+    nd = int(rng.integers(0, 3))
+    decim = tuple(int(rng.choice([1, 3, 8, 16, 32, 7, 64, 100])) for _ in range(nd))
+    amp = int(rng.integers(1, 200))
+    s = rng.integers(-amp, amp + 1, size=(F, C, X, N)).astype(np.int16)
+    if rng.random() < 0.3:                                  # extreme int16 values
+        s[rng.random(s.shape) < 0.01] = rng.choice([-32768, 32767])
+    spread = amp * np.sqrt(X)
+    T = int(rng.normal(0.3, 0.6) * spread)
+    params = dict(threshold=T, pre=pre, post=post, ped_samples=int(rng.integers(1, 150)), decim=decim)
+    fill_len = None
+    if rng.random() < 0.5:
+        fill_len = rng.integers(0, N + 1, size=F).astype(np.int32)
+        fill_len[rng.random(F) < 0.2] = N
+    tile = int(rng.choice([0, 128, 224, 448]))
+    return s, params, fill_len, tile
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_shapes(env, seed):
+    rng = np.random.default_rng(1000 + seed)
+    s, params, fill_len, tile = _random_case(rng)
+    hl = (params["post"] + 8) // 8 * 8
+    hr = (params["pre"] + 8) // 8 * 8
+    if tile and tile + hl + hr > 1024:
+        tile = 0
+    compare(env, s, params, fill_len=fill_len, tile=tile, grid=int(rng.choice([0, -1, 2])))
+
+
+def test_uneven_batch_of_fills(env):
+    from synth import workloads as W
+    w = W.scaled(W.BATCH_UNEVEN, n_calo=2)
+    fl, rate = w.plan()
+    s = env["synth"].generate(w.config(), fill_len=fl, rate=rate)
+    compare(env, s, w.params(), fill_len=fl)
+
+
+def test_stress_parameters(env):
+    from synth import workloads as W
+    w = W.scaled(W.STRESS, n_fills=2, n_calo=3)
+    s = env["synth"].generate(w.config())
+    res, ref = compare(env, s, w.params())
+    assert ref["n_rows"] > 0.95 * s.shape[0] * s.shape[1] * s.shape[3]   # heavy merging
+
+
+def test_degenerate_inputs(env):
+    params = dict(threshold=0, pre=2, post=3, ped_samples=4, decim=(8,))
+    rng = np.random.default_rng(5)
+    # all below threshold, all above, zero-length fills, single-sample fills
+    z = np.zeros((2, 2, 5, 1000), np.int16)
+    compare(env, z, params)
+    up = z.copy()
+    up[:, :, :, 4:] = 9
+    compare(env, up, params)
+    compare(env, rng.integers(-5, 6, size=(3, 2, 4, 640)).astype(np.int16), params, fill_len=[0, 1, 0])
+    compare(env, rng.integers(-5, 6, size=(1, 1, 54, 8)).astype(np.int16), params)
+
+
+def test_empty_batch(env):
+    torch, daq = env["torch"], env["daq"]
+    for shape in [(0, 24, 54, 1000), (2, 0, 54, 1000), (1, 2, 54, 0)]:
+        s = torch.zeros(shape, dtype=torch.int16, device="cuda")
+        res = daq.process_fills(s, hdr_cap=4, pool_cap=4)
+        assert res["status"] == daq.DAQ_OK
+        assert res["n_islands"] == 0 and res["n_rows"] == 0
+
+
+def test_capacity_overflow_reports_sizes_and_keeps_prefix(env):
+    torch, daq, oracle = env["torch"], env["daq"], env["oracle"]
+    from synth import workloads as W
+    w = W.scaled(W.PLAIN_FULL_FILL, n_calo=2, n_samples=30_000)
+    s = env["synth"].generate(w.config())
+    ref = oracle.process_fills(s, w.params())
+    hc, pc = ref["n_islands"] // 3, ref["n_rows"] // 2
+    q0 = torch.zeros(daq.q_size(2, 30_000, (32,)), dtype=torch.int64, device="cuda")
+    res = daq.process_fills(torch.from_numpy(s).cuda(), hdr_cap=hc, pool_cap=pc, q=q0, **w.params())
+    assert res["status"] == daq.DAQ_ECAPACITY
+    assert res["n_islands"] == ref["n_islands"] and res["n_rows"] == ref["n_rows"]
+    assert res["counts"][2] & (daq.DAQ_DEV_HDR_OVERFLOW | daq.DAQ_DEV_POOL_OVERFLOW)
+    out = res["outputs"]
+    assert np.array_equal(out.islands_host(hc), ref["islands"][:hc])
+    assert np.array_equal(out.pool[:pc].cpu().numpy(), ref["pool"][:pc])
+    assert np.array_equal(q0.cpu().numpy(), ref["q"])          # Q is accumulated exactly once
+
+
+def test_q_accumulates_across_calls_and_skip_flags(env):
+    torch, daq, oracle = env["torch"], env["daq"], env["oracle"]
+    from synth import workloads as W
+    w = W.scaled(W.STRESS, n_fills=1, n_calo=2, n_samples=50_000)
+    s = env["synth"].generate(w.config())
+    ref = oracle.process_fills(s, w.params())
+    ds = torch.from_numpy(s).cuda()
+    q = torch.zeros(daq.q_size(2, 50_000, (8, 32)), dtype=torch.int64, device="cuda")
+    daq.process_fills(ds, q=q, **w.params())
+    daq.process_fills(ds, q=q, flags=daq.DAQ_SKIP_ISLANDS, **w.params())
+    r3 = daq.process_fills(ds, q=q, flags=daq.DAQ_SKIP_Q, **w.params())
+    assert np.array_equal(q.cpu().numpy(), 2 * ref["q"])
+    assert r3["n_islands"] == ref["n_islands"]
+
+
+def test_fill_length_out_of_range_is_flagged(env):
+    torch, daq = env["torch"], env["daq"]
+    s = torch.zeros((2, 1, 3, 800), dtype=torch.int16, device="cuda")
+    fl = torch.tensor([900, -3], dtype=torch.int32, device="cuda")
+    with pytest.raises(daq.DaqError) as e:
+        daq.process_fills(s, fill_len=fl, hdr_cap=10, pool_cap=10)
+    assert e.value.status == daq.DAQ_EINVAL
+
+
+def test_full_fill_24_calorimeters(env):
+    """The benchmark workload itself (1.45 GB), full parity."""
+    from synth import workloads as W
+    w = W.PLAIN_FULL_FILL
+    s = env["synth"].generate(w.config())
+    compare(env, s, w.params(), n_threads=16)
