@@ -1,0 +1,430 @@
+#!/usr/bin/env python
+"""Benchmark of the muon g-2 waveform DAQ hot path (T-method islands + Q-method histograms).
+
+Default workload: one full fill, 24 calorimeters x 54 crystals x 560,000 int16
+samples (1.4515 GB), seeded synthetic waveforms, device-resident.  A step is
+one pass of the whole path over the fill: pedestals, crystal sum, threshold,
+pre/post windows, merge, island records + pool rows, Q decimation and the
+int64 fill-by-fill sum.  The input (1.45 GB) is larger than L2 (129 MB), so
+no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank processes its own fill
+on its own GPU (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "raw waveform GB/s (T+Q) and % of HBM peak; p99 per-fill latency"
+UNIT = "GB/s"
+NOMINAL_HBM_GBS = 7900.0
+
+
+# ----------------------------------------------------------------------------- helpers
+def measured_peaks() -> tuple:
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1611_04959_gb300", "csrc", "*.cu*")))
+    for fn in files:
+        h.update(open(fn, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    fn = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    if not os.path.exists(fn):
+        return None
+    kv = {}
+    for line in open(fn):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return float(kv["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """Samples SM clock and clock-event reasons through NVML (read-only) while
+    the timed region runs; falls back to `nvidia-smi -lms`."""
+    REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+               0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+    def __init__(self, index: int, period_s: float = 0.01):
+        self.index, self.period = index, period_s
+        self.samples, self.max_mhz, self._stop = [], None, threading.Event()
+        self._nvml = None
+        self._proc = None
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() == 0:
+                h = ctypes.c_void_p()
+                if nv.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(h)) == 0:
+                    self._nvml, self._h = nv, h
+                    mx = ctypes.c_uint()
+                    if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:  # NVML_CLOCK_SM
+                        self.max_mhz = int(mx.value)
+        except OSError:
+            self._nvml = None
+
+    def _run(self):
+        nv, h = self._nvml, self._h
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        get_r = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self._stop.is_set():
+            if nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and get_r(h, ctypes.byref(rs)) == 0:
+                self.samples.append((int(clk.value), int(rs.value)))
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self._nvml is not None:
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
+        else:
+            q = ("index,clocks.sm,clocks.max.sm,clocks_event_reasons.active")
+            self._proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                           "--format=csv,noheader,nounits", "-lms", "100"],
+                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        return self
+
+    def __exit__(self, *exc):
+        if self._nvml is not None:
+            self._stop.set()
+            self._t.join()
+        elif self._proc is not None:
+            self._proc.terminate()
+            out, _ = self._proc.communicate(timeout=10)
+            for line in out.splitlines():
+                try:
+                    _, sm, mx, act = [v.strip() for v in line.split(",")]
+                    self.samples.append((int(sm), int(act, 16)))
+                    self.max_mhz = int(mx)
+                except ValueError:
+                    pass
+
+    def summary(self) -> dict:
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0}
+        bits = 0
+        for _, r in self.samples:
+            bits |= r
+        names = [n for b, n in self.REASONS.items() if bits & b and n != "gpu_idle"]
+        return {"sm_mhz": statistics.median(s for s, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": names, "samples": len(self.samples)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------- CPU baseline (oracle)
+def run_cpu_oracle(samples_np, params, target_s: float, calos: int | None = None, length: int | None = None):
+    """Time the oracle, as it stands, on a bounded sample of the workload:
+    the first `calos` calorimeters x `length` samples, repeated until
+    target_s of CPU work.  Returns (GB/s, seconds, repeats, threads, bytes)."""
+    import numpy as np
+    import oracle
+    F, C, X, N = samples_np.shape
+    calos = calos or C
+    length = length or N
+    sub = np.ascontiguousarray(samples_np[:1, :calos, :, :length])
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.process_fills(sub, params, n_threads=threads)
+        reps += 1
+        if time.perf_counter() - t0 >= target_s:
+            break
+    dt = time.perf_counter() - t0
+    return reps * sub.nbytes / dt / 1e9, dt, reps, threads, sub.nbytes
+
+
+# ----------------------------------------------------------------------------- GB300 arm
+def bench_gb300(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_1611_04959_gb300 as daq
+    from paper_1611_04959_gb300 import build as daq_build
+    from synth import workloads as W
+
+    daq_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = W.PLAIN_FULL_FILL if args.calos == 24 else W.scaled(W.PLAIN_FULL_FILL, n_calo=args.calos)
+    params = w.params()
+    F, C, X, N = w.n_fills, w.n_calo, 54, w.n_samples
+    host = torch.empty((F, C, X, N), dtype=torch.int16).pin_memory()
+    synth.generate(w.config(), out=host.numpy(), n_threads=os.cpu_count() or 1)
+    samples = host.to(dev)
+    raw_bytes = samples.numel() * 2
+
+    stream = torch.cuda.Stream(dev)
+    rows_cap = F * C * N
+    out = daq.Outputs(torch, dev, F, C, X, rows_cap // 2 + F * C + 1, rows_cap)
+    q = torch.zeros(daq.q_size(C, N, params["decim"]), dtype=torch.int64, device=dev)
+
+    def make_p(grid=0):
+        p = daq.make_params(**params, stream=stream, grid=grid)
+        nbytes = daq.daq_workspace_size(C, X, N, F, p)
+        return p, nbytes
+
+    p, wsb = make_p()
+    workspace = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    p.workspace, p.workspace_bytes = workspace.data_ptr(), wsb
+    isl = out.struct()
+
+    def call(pp, ev_ptrs=None):
+        pp.events = ev_ptrs
+        rc = daq.daq_process_fills(samples.data_ptr(), C, X, N, F, pp, isl, q.data_ptr())
+        if rc != daq.DAQ_OK:
+            raise daq.DaqError(rc, "daq_process_fills")
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.zeros(1, device=dev)
+            dist.all_reduce(t)
+            torch.cuda.synchronize(dev)
+
+    # ---- warm-up
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            call(p)
+    torch.cuda.synchronize(dev)
+    counts = out.counts.cpu().numpy()
+    status = daq.daq_status_from_counts(counts)
+    if status != daq.DAQ_OK:
+        raise daq.DaqError(status, "warm-up")
+    n_isl, n_rows = int(counts[0]), int(counts[1])
+
+    # ---- timed region: K steps, three events per step (pedestal start, tile start, tile end)
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    for trio in evs:                      # creates the events before their handles are taken
+        for e in trio:
+            e.record(stream)
+    ev_arrays = [(ctypes.c_void_p * 3)(*[e.cuda_event for e in trio]) for trio in evs]
+    barrier()
+    with ClockSampler(local) as clocks:
+        with torch.cuda.stream(stream):
+            for k in range(K):
+                call(p, ctypes.cast(ev_arrays[k], ctypes.c_void_p).value)
+        torch.cuda.synchronize(dev)
+    elapsed_ms = evs[0][0].elapsed_time(evs[-1][2])
+    step_ms = [trio[0].elapsed_time(trio[2]) for trio in evs]
+    tile_ms = [trio[1].elapsed_time(trio[2]) for trio in evs]
+    prep_ms = [trio[0].elapsed_time(trio[1]) for trio in evs]
+    t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed_ms = float(t.item())
+    value = K * raw_bytes * ws / (elapsed_ms * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel (daq_tile_kernel)
+    peak, peak_kind = measured_peaks()
+    q_bytes = sum(C * daq.daq_q_bins(N, d) * 16 for d in params["decim"])
+    alg_bytes = raw_bytes + n_rows * X * 2 + n_isl * 24 + q_bytes
+    tile_mean_ms = statistics.fmean(tile_ms)
+    achieved = alg_bytes / (tile_mean_ms * 1e-3) / 1e9
+    traffic = profiled_traffic("daq_tile_kernel", "full_fill")
+
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(elapsed_ms / K, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"full fill: {C} calorimeters x 54 crystals x 560,000 int16 samples "
+                               f"({raw_bytes / 1e9:.4f} GB), literal noise sigma 3/crystal, T=30, pre=8, post=24, D=32",
+                   "fills_per_step_per_gpu": 1, "raw_bytes_per_step_per_gpu": raw_bytes,
+                   "l2": "inputs larger than L2 (1.45 GB per step vs 129 MB)", "parallelism": f"replicas x{ws}",
+                   "tile": 448, "grid": "persistent"},
+        "pct_of_hbm_peak": round(100.0 * value / ws / peak, 2),
+        "pct_of_nominal_hbm": round(100.0 * value / ws / NOMINAL_HBM_GBS, 2),
+        "latency_ms": {"p50": round(statistics.median(step_ms), 4),
+                       "p99": round(float(np.percentile(step_ms, 99)), 4),
+                       "max": round(max(step_ms), 4)},
+        "kernels_ms": {"daq_prepare_kernel": round(statistics.fmean(prep_ms), 4),
+                       "daq_tile_kernel": round(tile_mean_ms, 4)},
+        "islands_per_fill": n_isl, "pool_rows_per_fill": n_rows,
+        "coverage": round(n_rows / (C * N), 4),
+        "output_over_input": round((n_rows * X * 2 + n_isl * 24) / raw_bytes, 4),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
+                     "kernel": "daq_tile_kernel", "algorithmic_bytes_per_launch": alg_bytes},
+        "gpu_launches": 2 * K,
+        "clocks": clocks.summary(),
+    }
+
+    # ---- plain form: one CTA per tile, no persistence
+    if not args.quick:
+        pp, _ = make_p(grid=-1)
+        pp.workspace, pp.workspace_bytes = workspace.data_ptr(), wsb
+        Kp = max(3, min(K, 200))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                call(pp)
+            e0.record(stream)
+            for _ in range(Kp):
+                call(pp)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        result["plain_form"] = {"value": round(Kp * raw_bytes / (e0.elapsed_time(e1) * 1e-3) / 1e9, 2),
+                                "unit": UNIT, "steps": Kp, "grid": "one CTA per tile"}
+
+    # ---- end to end through the host-buffer entry point
+    if not args.no_e2e:
+        hdr_h = torch.empty(out.hdr_cap * 3, dtype=torch.int64).pin_memory()
+        pool_h = torch.empty((rows_cap, X), dtype=torch.int16).pin_memory()
+        counts_h = torch.zeros(4, dtype=torch.int64)
+        io = daq.DaqHostIO(host.data_ptr(), samples.data_ptr(), hdr_h.data_ptr(), out.hdr_cap, pool_h.data_ptr(),
+                           rows_cap, None, counts_h.data_ptr())
+        pe, _ = make_p()
+        pe.workspace, pe.workspace_bytes = workspace.data_ptr(), wsb
+        Ke = max(3, min(K, args.e2e_steps))
+        for _ in range(2):
+            rc = daq.daq_process_fills_host(C, X, N, F, pe, isl, q.data_ptr(), io)
+            assert rc == daq.DAQ_OK, rc
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for _ in range(Ke):
+            daq.daq_process_fills_host(C, X, N, F, pe, isl, q.data_ptr(), io)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ems = e0.elapsed_time(e1)
+        te = torch.tensor([ems], device=dev, dtype=torch.float64)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        ems = float(te.item())
+        d2h = 32 + int(counts_h[0]) * 24 + int(counts_h[1]) * X * 2
+        result["e2e"] = {"value": round(Ke * raw_bytes * ws / (ems * 1e-3) / 1e9, 2), "unit": UNIT,
+                         "h2d_bytes_per_step": raw_bytes, "d2h_bytes_per_step": d2h, "steps": Ke,
+                         "ms_per_step": round(ems / Ke, 3),
+                         "api": "daq_process_fills_host (pinned host buffers)"}
+
+    # ---- CPU baseline: the oracle on a bounded sample of the same fill (rank 0)
+    if rank == 0 and not args.no_cpu_baseline:
+        gbs, dt, reps, threads, nbytes = run_cpu_oracle(host.numpy(), params, args.cpu_seconds)
+        result["cpu_baseline"] = {"value": round(gbs, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+                                  "sample": f"the whole 24-calorimeter fill ({nbytes} B) x {reps} passes, "
+                                            f"{dt:.1f} s, calorimeter-fills spread over {threads} host threads"}
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return result if rank == 0 else None
+
+
+# ----------------------------------------------------------------------------- reference arm (oracle)
+def bench_reference(args, ws, rank, local):
+    if rank != 0:
+        return None
+    import numpy as np
+    import oracle
+    import synth
+    from synth import workloads as W
+    oracle.build()
+    w = W.PLAIN_FULL_FILL
+    params = w.params()
+    threads = os.cpu_count() or 1
+    calos = min(w.n_calo, threads)
+    cfg = W.scaled(w, n_calo=calos).config()
+    s = synth.generate(cfg, n_threads=threads)
+    # bounded sample per step: `calos` calorimeters x `length` samples, sized so
+    # that warm-up + timed steps end within about two minutes
+    budget = max(0.05, min(2.0, 120.0 / max(1, args.steps + args.warmup)))
+    t0 = time.perf_counter()
+    oracle.process_fills(np.ascontiguousarray(s[:, :, :, :56_000]), params, n_threads=threads)
+    per_sample = (time.perf_counter() - t0) / 56_000
+    length = int(min(w.n_samples, max(4_000, budget / max(per_sample, 1e-12))) // 8 * 8)
+    sub = np.ascontiguousarray(s[:, :, :, :length])
+    for _ in range(args.warmup):
+        oracle.process_fills(sub, params, n_threads=threads)
+    times = []
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        oracle.process_fills(sub, params, n_threads=threads)
+        times.append(time.perf_counter() - t1)
+    total = sum(times)
+    value = len(times) * sub.nbytes / total / 1e9
+    sample = f"{calos} calorimeters x 54 crystals x first {length} samples of the fill per step ({sub.nbytes} B)"
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / len(times), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "full fill: 24 calorimeters x 54 crystals x 560,000 int16 samples (1.4515 GB), "
+                               "literal noise sigma 3/crystal, T=30, pre=8, post=24, D=32",
+                   "sample_per_step": sample},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the plain-form comparison")
+    ap.add_argument("--calos", type=int, default=24, help="calorimeters per fill (24; fewer only for profiling)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        res = bench_reference(args, ws, rank, local)
+    else:
+        res = bench_gb300(args, ws, rank, local)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

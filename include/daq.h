@@ -91,6 +91,9 @@ typedef struct daq_island {
  *   workspace    device scratch of at least daq_workspace_size() bytes,
  *                16-byte aligned; reused by the call and not to be shared by
  *                calls that may run at the same time.
+ *   events       NULL, or a host array of three cudaEvent_t that the call
+ *                records on `stream` before the pedestal kernel, between the
+ *                two kernels and after the tile kernel (per-kernel timing).
  */
 typedef struct daq_params {
     int32_t threshold;
@@ -108,6 +111,7 @@ typedef struct daq_params {
     void *stream;
     void *workspace;
     size_t workspace_bytes;
+    void *const *events;
 } daq_params;
 
 /*
@@ -166,6 +170,40 @@ int64_t daq_q_bins(int64_t n_samples, int32_t decim);
  */
 int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_samples, int n_fills,
                       const daq_params *params, const daq_islands *islands_out, int64_t *qhist_inout);
+
+/*
+ * Host buffers of daq_process_fills_host (the end-to-end form).
+ *   samples_host   host int16[n_fills][n_calo][n_xtal][n_samples]; page-locked
+ *                  memory gives full copy bandwidth.
+ *   samples_dev    device buffer of the same size that receives the copy.
+ *   hdr_host, pool_host, pedestal_host  host buffers that receive the island
+ *                  records, pool rows and pedestals (pedestal_host may be NULL);
+ *                  at most *_cap entries are copied.
+ *   counts_host    host int64[4], receives counts (see daq_islands).
+ */
+typedef struct daq_host_io {
+    const int16_t *samples_host;
+    int16_t *samples_dev;
+    daq_island *hdr_host;
+    int64_t hdr_host_cap;
+    int16_t *pool_host;
+    int64_t pool_host_cap;
+    int32_t *pedestal_host;
+    int64_t *counts_host;
+} daq_host_io;
+
+/*
+ * End-to-end form over host buffers, as the paper's GPU thread does it (Sec. 3:
+ * copy one fill to the GPU, process it, return the chopped islands to host
+ * memory).  Copies io->samples_host to io->samples_dev on params->stream, runs
+ * daq_process_fills with the device outputs in islands_dev, then copies the
+ * counts, island records, pool rows and (if requested) pedestals back.  The Q
+ * histograms stay on the device (qhist_inout).  Waits for the stream before
+ * returning; returns the call's status (DAQ_ECAPACITY if a device or host
+ * capacity was short: counts_host then holds the sizes needed).
+ */
+int daq_process_fills_host(int n_calo, int n_xtal, int64_t n_samples, int n_fills, const daq_params *params,
+                           const daq_islands *islands_dev, int64_t *qhist_inout, const daq_host_io *io);
 
 /* Map a host copy of counts[4] to a daq_status (DAQ_OK if no bit is set). */
 int daq_status_from_counts(const int64_t *counts_host);

@@ -32,12 +32,18 @@ class DaqParams(ctypes.Structure):
                 ("fill_base", ctypes.c_int32), ("fill_len", ctypes.c_void_p), ("flags", ctypes.c_uint32),
                 ("tile", ctypes.c_int32), ("grid", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("events", ctypes.c_void_p)]
 
 
 class DaqIslands(ctypes.Structure):
     _fields_ = [("hdr", ctypes.c_void_p), ("hdr_cap", ctypes.c_int64), ("pool", ctypes.c_void_p),
                 ("pool_row_cap", ctypes.c_int64), ("pedestal", ctypes.c_void_p), ("counts", ctypes.c_void_p)]
+
+
+class DaqHostIO(ctypes.Structure):
+    _fields_ = [("samples_host", ctypes.c_void_p), ("samples_dev", ctypes.c_void_p), ("hdr_host", ctypes.c_void_p),
+                ("hdr_host_cap", ctypes.c_int64), ("pool_host", ctypes.c_void_p), ("pool_host_cap", ctypes.c_int64),
+                ("pedestal_host", ctypes.c_void_p), ("counts_host", ctypes.c_void_p)]
 
 
 class DaqError(RuntimeError):
@@ -69,6 +75,9 @@ def lib():
             L.daq_process_fills.argtypes = [vp, i32, i32, i64, i32, ctypes.POINTER(DaqParams),
                                             ctypes.POINTER(DaqIslands), vp]
             L.daq_process_fills.restype = i32
+            L.daq_process_fills_host.argtypes = [i32, i32, i64, i32, ctypes.POINTER(DaqParams),
+                                                 ctypes.POINTER(DaqIslands), vp, ctypes.POINTER(DaqHostIO)]
+            L.daq_process_fills_host.restype = i32
             L.daq_status_from_counts.argtypes = [vp]
             L.daq_status_from_counts.restype = i32
             L.daq_strerror.argtypes = [i32]
@@ -106,6 +115,12 @@ def daq_process_fills(samples_ptr: int, n_calo: int, n_xtal: int, n_samples: int
                       params: DaqParams, islands: DaqIslands, qhist_ptr: int | None) -> int:
     return int(lib().daq_process_fills(samples_ptr, n_calo, n_xtal, n_samples, n_fills, ctypes.byref(params),
                                        ctypes.byref(islands), qhist_ptr))
+
+
+def daq_process_fills_host(n_calo: int, n_xtal: int, n_samples: int, n_fills: int, params: DaqParams,
+                           islands_dev: DaqIslands, qhist_ptr: int | None, io: DaqHostIO) -> int:
+    return int(lib().daq_process_fills_host(n_calo, n_xtal, n_samples, n_fills, ctypes.byref(params),
+                                            ctypes.byref(islands_dev), qhist_ptr, ctypes.byref(io)))
 
 
 def daq_status_from_counts(counts_host) -> int:

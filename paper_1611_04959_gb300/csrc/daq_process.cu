@@ -860,7 +860,9 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
         if ((reinterpret_cast<uintptr_t>(out->pool) & 15) || (reinterpret_cast<uintptr_t>(out->hdr) & 7))
             return DAQ_EINVAL;
     }
-    if (!skip_q && p.n_decim > 0 && !qhist_inout) return DAQ_EINVAL;
+    int64_t q_total = 0;
+    for (int d = 0; d < p.n_decim; ++d) q_total += q_bins(n_samples, p.decim[d]) * n_calo;
+    if (!skip_q && q_total > 0 && !qhist_inout) return DAQ_EINVAL;
     if (reinterpret_cast<uintptr_t>(out->counts) & 7) return DAQ_EINVAL;
     const WsLayout wl = ws_layout(n_fills, n_calo, pl.max_tiles);
     if (!p.workspace || p.workspace_bytes < wl.total || (reinterpret_cast<uintptr_t>(p.workspace) & 15))
@@ -916,10 +918,13 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
     if (di.sms <= 0) return DAQ_ECUDA;
     if ((int)pl.smem > di.smem_optin) return DAQ_EUNSUPPORTED;
 
+    cudaEvent_t const *ev = reinterpret_cast<cudaEvent_t const *>(p.events);
+    if (ev && cudaEventRecord(ev[0], s) != cudaSuccess) return DAQ_ECUDA;
     const long long n_cf = (long long)n_fills * n_calo;
     const int prep_grid = (int)std::max<long long>(1, std::min<long long>(std::max<long long>(n_cf, 1), 4ll * di.sms));
     daq_prepare_kernel<<<prep_grid, kThreads, 0, s>>>(a, pl.tw);
     if (cudaGetLastError() != cudaSuccess) return DAQ_ECUDA;
+    if (ev && cudaEventRecord(ev[1], s) != cudaSuccess) return DAQ_ECUDA;
 
     int grid = p.grid;
     if (grid < 0) grid = (int)std::max<int64_t>(1, std::min<int64_t>(pl.max_tiles, INT32_MAX));
@@ -933,6 +938,7 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
     default: e = launch_tile<960>(a, pl, grid, s); break;
     }
     if (e != cudaSuccess) return DAQ_ECUDA;
+    if (ev && cudaEventRecord(ev[2], s) != cudaSuccess) return DAQ_ECUDA;
 
     if (p.flags & DAQ_SYNC) {
         if (cudaStreamSynchronize(s) != cudaSuccess) return DAQ_ECUDA;

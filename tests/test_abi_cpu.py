@@ -38,8 +38,8 @@ def test_every_declared_symbol_is_exported(daq):
 
 
 def test_struct_layouts_match_header(daq):
-    # daq_params: 8 int32, pointer, uint32 + 3 int32, 2 pointers, size_t
-    assert ctypes.sizeof(daq.DaqParams) == 32 + 8 + 16 + 8 + 8 + 8
+    # daq_params: 8 int32, pointer, uint32 + 3 int32, 2 pointers, size_t, pointer
+    assert ctypes.sizeof(daq.DaqParams) == 32 + 8 + 16 + 8 + 8 + 8 + 8
     assert ctypes.sizeof(daq.DaqIslands) == 6 * 8
     assert daq.ISLAND_DTYPE.itemsize == 24
 
