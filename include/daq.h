@@ -83,10 +83,12 @@ typedef struct daq_island {
  *                NULL for n_samples each.  Out-of-range values are clamped and
  *                flagged with DAQ_DEV_BAD_FILL_LEN.
  *   flags        DAQ_SKIP_Q | DAQ_SKIP_ISLANDS | DAQ_SYNC.
- *   tile         samples per tile: 0 = default (448); else 128, 224, 448 or 960.
- *   grid         CTAs: 0 = persistent (resident CTAs per SM x SMs);
- *                -1 = one CTA per tile (the plain, non-persistent form);
- *                > 0 = exactly this many persistent CTAs.
+ *   tile         samples per tile: 0 = default (448, or the largest of 224 and
+ *                128 whose shared-memory plan fits); else 128, 224, 448 or 960.
+ *   grid         0  = pipelined persistent kernel, one CTA per SM (default);
+ *                > 0 = pipelined kernel with exactly this many CTAs;
+ *                -1 = plain kernel, one CTA per tile (non-persistent form);
+ *                -2 = plain kernel, persistent (resident CTAs per SM x SMs).
  *   stream       cudaStream_t (NULL = legacy default stream).
  *   workspace    device scratch of at least daq_workspace_size() bytes,
  *                16-byte aligned; reused by the call and not to be shared by

@@ -1,0 +1,553 @@
+// Per-tile steps of the fused DAQ kernels (Sec. 3, Table 2 of arXiv:1611.04959),
+// shared by the simple and the pipelined tile kernels.
+//
+// A tile is TW consecutive samples [t0, t0 + TW) of one calorimeter-fill.  Its
+// crystal rows are held in shared memory with a halo: column c of a row is
+// sample t0 - HL + c, for c in [0, EW), EW = HL + TW + HR.  Row stride RS is an
+// odd multiple of 16 bytes, so the eight rows of every ldmatrix are
+// conflict-free.
+#pragma once
+
+#include <cstdint>
+
+#include "daq.h"
+#include "daq_device.cuh"
+
+namespace daq {
+
+constexpr uint64_t kWaitLimitNs = 4000000000ull;  // bounded device waits (4 s)
+constexpr int kMaxXtal = 64;
+constexpr int kMaxExtBits = 1024;  // tile + halos: one warp of 32-bit words
+
+// Scan state of one tile: aggregate and inclusive prefix, each a (flag, payload) pair.
+// flag word  = (marked samples << 2) | kind, kind 1 = valid, 2 = poisoned
+// payload    = (island starts << 32) | (trailing run << 1) | continues
+struct TileStatus {
+    unsigned long long agg_payload, agg_flag;
+    unsigned long long inc_payload, inc_flag;
+};
+
+struct Agg {
+    long long m;   // marked samples (pool rows)
+    long long s;   // island starts
+    long long tr;  // marked samples in the run that ends at the tile's last sample
+    int full;      // every sample marked and the run continues from the previous tile
+    int poison;
+};
+
+__device__ __forceinline__ Agg agg_identity() { return Agg{0, 0, 0, 1, 0}; }
+
+// Prefix p followed by tile t (associative, not commutative).
+__device__ __forceinline__ Agg combine(const Agg &p, const Agg &t)
+{
+    Agg r;
+    r.m = p.m + t.m;
+    r.s = p.s + t.s;
+    r.tr = t.full ? p.tr + t.tr : t.tr;
+    r.full = p.full && t.full;
+    r.poison = p.poison | t.poison;
+    return r;
+}
+
+__device__ __forceinline__ Agg shfl_agg(const Agg &a, int src)
+{
+    Agg r;
+    r.m = __shfl_sync(kFull, a.m, src);
+    r.s = __shfl_sync(kFull, a.s, src);
+    r.tr = __shfl_sync(kFull, a.tr, src);
+    r.full = __shfl_sync(kFull, a.full, src);
+    r.poison = __shfl_sync(kFull, a.poison, src);
+    return r;
+}
+
+__device__ __forceinline__ Agg shfl_down_agg(const Agg &a, int d)
+{
+    Agg r;
+    r.m = __shfl_down_sync(kFull, a.m, d);
+    r.s = __shfl_down_sync(kFull, a.s, d);
+    r.tr = __shfl_down_sync(kFull, a.tr, d);
+    r.full = __shfl_down_sync(kFull, a.full, d);
+    r.poison = __shfl_down_sync(kFull, a.poison, d);
+    return r;
+}
+
+struct KArgs {
+    const int16_t *samples;
+    int32_t n_calo, n_xtal, n_fills;
+    int64_t n_samples;  // row pitch
+    int32_t threshold, pre, post, ped_samples;
+    int32_t n_decim, decim[2];
+    int64_t qbins[2], qoff[2];
+    int32_t fill_base;
+    const int32_t *fill_len;
+    uint32_t flags;
+    int32_t hl, hr, ew, rs;  // halo left/right, extended width, smem row stride (bytes)
+    int32_t bulk_ok;
+    int32_t need_sarr;
+    int64_t max_tiles;
+    // outputs
+    daq_island *hdr;
+    int64_t hdr_cap;
+    int16_t *pool;
+    int64_t pool_cap;
+    int32_t *ped_out;
+    int64_t *counts;
+    int64_t *q;
+    // workspace
+    unsigned int *ticket;
+    long long *fill_tile_start;  // [n_fills + 1]
+    int32_t *lens;               // [n_fills], clamped
+    int32_t *ptot;               // [n_fills * n_calo]
+    TileStatus *status;          // [max_tiles]
+};
+
+struct TileInfo {
+    long long tile;  // -1: no more tiles
+    long long t0, len, t_end;
+    int f, c, ptot, pad;
+};
+
+// Bit words of the tile proper and their prefix counts.
+struct TileWords {
+    uint32_t *m, *s, *e;  // marked, island starts, island ends
+    int32_t *mb, *sb;     // marked / starts before the word
+    int32_t *ls;          // last island start before the word (tile-relative), -1
+};
+
+__device__ __forceinline__ void set_status_bit(const KArgs &a, unsigned long long bit)
+{
+    atomicOr(reinterpret_cast<unsigned long long *>(&a.counts[2]), bit);
+}
+
+__device__ __forceinline__ bool aborted(const KArgs &a)
+{
+    return (ld_relaxed_u64(reinterpret_cast<const unsigned long long *>(&a.counts[2])) & DAQ_DEV_TIMEOUT) != 0;
+}
+
+// Map a ticket to its tile.  Tiles are numbered fill by fill, calorimeter by
+// calorimeter, then in time; a fill of length len has ceil(len / TW) tiles
+// per calorimeter.
+template <int TW> __device__ bool decode_tile(const KArgs &a, long long tile, TileInfo &T)
+{
+    const long long total = a.fill_tile_start[a.n_fills];
+    T.tile = -1;
+    if (tile >= total) return false;
+    int lo = 0, hi = a.n_fills - 1;  // last fill whose first tile <= tile
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.fill_tile_start[mid] <= tile) lo = mid; else hi = mid - 1;
+    }
+    const long long len = a.lens[lo];
+    const long long tpc = (len + TW - 1) / TW;
+    const long long rem = tile - a.fill_tile_start[lo];
+    T.tile = tile;
+    T.f = lo;
+    T.c = (int)(rem / tpc);
+    T.t0 = (rem % tpc) * TW;
+    T.len = len;
+    T.t_end = T.t0 + TW < len ? T.t0 + TW : len;
+    T.ptot = a.ptot[(long long)lo * a.n_calo + T.c];
+    T.pad = 0;
+    return true;
+}
+
+// --------------------------------------------------------------------------- crystal sum + threshold
+// One 8-sample block b of the extended tile (warp-wide).  Lane L of the
+// ldmatrix transposes holds crystals 8g + 2(L%4), +1 at sample L/4 of the block;
+// dp2a adds both halves, two shuffles finish the 54-crystal sum.
+__device__ __forceinline__ void sum_block(const KArgs &a, const TileInfo &T, uint32_t a_lo, uint32_t a_hi,
+                                          bool two_groups, int b, int nbt, uint8_t *abyte, int32_t *blocksum,
+                                          int32_t *sarr, int lane)
+{
+    const uint32_t col = 16u * (uint32_t)b;
+    uint32_t r0, r1, r2, r3, r4 = 0, r5 = 0, r6 = 0, r7 = 0;
+    ldsm_x4_trans(a_lo + col, r0, r1, r2, r3);
+    if (two_groups) ldsm_x4_trans(a_hi + col, r4, r5, r6, r7);
+    int acc = __dp2a_lo((int)r0, 0x0101, 0);
+    acc = __dp2a_lo((int)r1, 0x0101, acc);
+    acc = __dp2a_lo((int)r2, 0x0101, acc);
+    acc = __dp2a_lo((int)r3, 0x0101, acc);
+    acc = __dp2a_lo((int)r4, 0x0101, acc);
+    acc = __dp2a_lo((int)r5, 0x0101, acc);
+    acc = __dp2a_lo((int)r6, 0x0101, acc);
+    acc = __dp2a_lo((int)r7, 0x0101, acc);
+    acc += __shfl_xor_sync(kFull, acc, 1);
+    acc += __shfl_xor_sync(kFull, acc, 2);
+    const int j = lane >> 2;
+    const long long t = T.t0 - a.hl + 8 * b + j;
+    const int S = acc - T.ptot;
+    const bool cross = (t >= 0) && (t < T.len) && (S > a.threshold);
+    uint32_t v = __ballot_sync(kFull, cross) & 0x11111111u;
+    v = (v | (v >> 3)) & 0x03030303u;
+    v = (v | (v >> 6)) & 0x000f000fu;
+    v = (v | (v >> 12)) & 0xffu;
+    if (lane == 0) abyte[b] = (uint8_t)v;
+    const int bt = b - a.hl / 8;
+    if (bt >= 0 && bt < nbt) {
+        const bool in = t < T.t_end;
+        int sv = in ? S : 0;
+        sv += __shfl_xor_sync(kFull, sv, 4);
+        sv += __shfl_xor_sync(kFull, sv, 8);
+        sv += __shfl_xor_sync(kFull, sv, 16);
+        if (lane == 0) blocksum[bt] = sv;
+        if (a.need_sarr && (lane & 3) == 0 && in) sarr[8 * bt + j] = S;
+    }
+}
+
+// --------------------------------------------------------------------------- windows + merge (one warp)
+// From the threshold bits of the extended tile: marks M (crossings widened by
+// pre/post samples), island starts and ends inside the tile, prefix counts per
+// word, and the tile's aggregate for the cross-tile scan.
+template <int TW>
+__device__ __forceinline__ Agg tile_bits(const KArgs &a, const TileInfo &T, const uint8_t *abyte, TileWords w,
+                                         int lane)
+{
+    constexpr int NWT = TW / 32;
+    const int HL = a.hl;
+    const int NWE = (a.ew + 31) / 32;
+    const long long e0 = T.t0 - HL;
+    const uint32_t A = lane < NWE ? reinterpret_cast<const uint32_t *>(abyte)[lane] : 0u;
+    // forward spread: F[i] = OR_{k=0..post} A[i-k]
+    uint32_t Fv = A;
+    int cov = 1;
+    while (2 * cov <= a.post + 1) {
+        Fv |= shl_bits(Fv, cov, lane);
+        cov *= 2;
+    }
+    if (cov < a.post + 1) Fv |= shl_bits(Fv, a.post + 1 - cov, lane);
+    // backward spread: M[i] = OR_{k=0..pre} F[i+k]
+    uint32_t Mv = Fv;
+    cov = 1;
+    while (2 * cov <= a.pre + 1) {
+        Mv |= shr_bits(Mv, cov, lane);
+        cov *= 2;
+    }
+    if (cov < a.pre + 1) Mv |= shr_bits(Mv, a.pre + 1 - cov, lane);
+    Mv &= range_mask(32ll * lane, -e0, T.len - e0);  // only samples of [0, len) are marked
+    const uint32_t m_prev = (__shfl_sync(kFull, Mv, (HL - 1) >> 5) >> ((HL - 1) & 31)) & 1u;
+    const uint32_t m_next = (__shfl_sync(kFull, Mv, (HL + TW) >> 5) >> ((HL + TW) & 31)) & 1u;
+    const int qo = HL >> 5, sh = HL & 31;
+    uint32_t lo_w = __shfl_down_sync(kFull, Mv, qo);
+    uint32_t hi_w = __shfl_down_sync(kFull, Mv, qo + 1 < 32 ? qo + 1 : 31);
+    if (lane + qo > 31) lo_w = 0u;
+    if (lane + qo + 1 > 31) hi_w = 0u;
+    uint32_t Mt = sh ? ((lo_w >> sh) | (hi_w << (32 - sh))) : lo_w;
+    if (lane >= NWT) Mt = 0u;
+    uint32_t below = __shfl_up_sync(kFull, Mt, 1);
+    if (lane == 0) below = m_prev << 31;
+    uint32_t above = __shfl_down_sync(kFull, Mt, 1);
+    if (lane == NWT - 1) above = m_next;
+    if (lane >= NWT) above = 0u;
+    const uint32_t St = Mt & ~((Mt << 1) | (below >> 31));
+    const uint32_t Et = Mt & ~((Mt >> 1) | (above << 31));
+    int m_tot, s_tot;
+    const int mb = warp_excl_scan_add<int>(__popc(Mt), lane, m_tot);
+    const int sb = warp_excl_scan_add<int>(__popc(St), lane, s_tot);
+    const int last_start = St ? 32 * lane + 31 - __clz(St) : -1;
+    const int ls = warp_excl_scan_max(last_start, lane, -1);
+    const int nt = (int)(T.t_end - T.t0);
+    const uint32_t zeros = ~Mt & range_mask(32ll * lane, 0, nt);
+    const int lz = warp_max(zeros ? 32 * lane + 31 - __clz(zeros) : -1);
+    if (lane < NWT) {
+        w.m[lane] = Mt;
+        w.s[lane] = St;
+        w.e[lane] = Et;
+        w.mb[lane] = mb;
+        w.sb[lane] = sb;
+        w.ls[lane] = ls;
+    }
+    Agg agg;
+    agg.m = m_tot;
+    agg.s = s_tot;
+    agg.tr = nt - 1 - lz;
+    agg.full = (lz < 0) && m_prev;
+    agg.poison = 0;
+    return agg;
+}
+
+// --------------------------------------------------------------------------- cross-tile scan
+__device__ __forceinline__ void publish(TileStatus *st, long long tile, bool inclusive, const Agg &v)
+{
+    const unsigned long long flag = ((unsigned long long)v.m << 2) | (v.poison ? 2ull : 1ull);
+    const unsigned long long payload =
+        ((unsigned long long)v.s << 32) | ((unsigned long long)v.tr << 1) | (unsigned long long)(v.full != 0);
+    if (inclusive) {
+        st_relaxed_u64(&st[tile].inc_payload, payload);
+        st_release_u64(&st[tile].inc_flag, flag);
+    } else {
+        st_relaxed_u64(&st[tile].agg_payload, payload);
+        st_release_u64(&st[tile].agg_flag, flag);
+    }
+}
+
+__device__ __forceinline__ Agg decode_status(unsigned long long flag, unsigned long long payload)
+{
+    Agg r;
+    r.m = (long long)(flag >> 2);
+    r.poison = (flag & 3ull) == 2ull;
+    r.s = (long long)(payload >> 32);
+    r.tr = (long long)((payload >> 1) & 0x7fffffffull);
+    r.full = (int)(payload & 1ull);
+    return r;
+}
+
+// Decoupled look-back (one warp): exclusive prefix of `tile` over all earlier
+// tiles.  Each round reads 128 predecessors (4 per lane), stops at the nearest
+// inclusive prefix, and combines aggregates in order.  Bounded: gives up after
+// kWaitLimitNs or when another CTA has flagged a timeout, returning a poisoned
+// prefix.
+__device__ Agg look_back(const KArgs &a, long long tile, int lane)
+{
+    constexpr int PER = 4;
+    const TileStatus *st = a.status;
+    long long pos = tile - 1;
+    Agg acc = agg_identity();
+    uint64_t t_start = 0;
+    bool waiting = false;
+    for (uint32_t iter = 0;; ++iter) {
+        int kind[PER];
+        Agg v[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const long long idx = pos - (PER * lane + j);
+            kind[j] = 2;
+            v[j] = agg_identity();
+            if (idx >= 0) {
+                kind[j] = 0;
+                unsigned long long fl = ld_acquire_u64(&st[idx].inc_flag);
+                if (fl & 3ull) {
+                    kind[j] = 2;
+                    v[j] = decode_status(fl, ld_relaxed_u64(&st[idx].inc_payload));
+                } else {
+                    fl = ld_acquire_u64(&st[idx].agg_flag);
+                    if (fl & 3ull) {
+                        kind[j] = 1;
+                        v[j] = decode_status(fl, ld_relaxed_u64(&st[idx].agg_payload));
+                    }
+                }
+            }
+        }
+        // nearest inclusive prefix g = PER * lane + j
+        int first_inc = 1 << 30, first_missing = 1 << 30;
+#pragma unroll
+        for (int j = PER - 1; j >= 0; --j) {
+            if (kind[j] == 2) first_inc = PER * lane + j;
+            if (kind[j] == 0) first_missing = PER * lane + j;
+        }
+        int stop = first_inc, missing = first_missing;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            stop = min(stop, __shfl_xor_sync(kFull, stop, d));
+            missing = min(missing, __shfl_xor_sync(kFull, missing, d));
+        }
+        const int last_needed = stop < (1 << 30) ? stop : 32 * PER - 1;
+        if (missing <= last_needed) {
+            // a needed predecessor has published nothing yet: wait (bounded)
+            if (!waiting) {
+                t_start = global_ns();
+                waiting = true;
+            }
+            if ((iter & 15u) == 15u) {
+                int give_up = lane == 0 && (global_ns() - t_start > kWaitLimitNs || aborted(a));
+                if (__shfl_sync(kFull, give_up, 0)) {
+                    acc.poison = 1;
+                    if (lane == 0) set_status_bit(a, DAQ_DEV_TIMEOUT);
+                    return acc;
+                }
+            }
+            __nanosleep(32);
+            continue;
+        }
+        // this lane's entries up to last_needed, in order (latest last)
+        Agg lane_acc = agg_identity();
+#pragma unroll
+        for (int j = PER - 1; j >= 0; --j)
+            if (PER * lane + j <= last_needed) lane_acc = combine(lane_acc, v[j]);
+        // ordered reduction over lanes: higher lanes hold earlier tiles
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const Agg other = shfl_down_agg(lane_acc, d);
+            if ((lane & (2 * d - 1)) == 0 && lane + d < 32) lane_acc = combine(other, lane_acc);
+        }
+        const Agg window = shfl_agg(lane_acc, 0);
+        acc = combine(window, acc);
+        if (stop < (1 << 30)) return acc;
+        pos -= 32 * PER;
+        waiting = false;
+    }
+}
+
+// --------------------------------------------------------------------------- staging of pool rows
+// Block bt of the tile proper (warp-wide): every marked sample's n_xtal raw
+// values go to its row in the tile-local stage area (row = marked samples
+// before it in the tile).
+__device__ __forceinline__ void stage_block(const KArgs &a, uint32_t a_lo, uint32_t a_hi, bool two_groups, int bt,
+                                            const uint32_t *w_m, const int32_t *w_mb, unsigned char *stage,
+                                            int lane)
+{
+    const int X = a.n_xtal;
+    const int w = bt >> 2, shift = (bt & 3) * 8;
+    const uint32_t mw = w_m[w];
+    const uint32_t bits = (mw >> shift) & 0xffu;
+    if (!bits) return;
+    const uint32_t col = 16u * (uint32_t)(bt + a.hl / 8);
+    uint32_t r[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    ldsm_x4_trans(a_lo + col, r[0], r[1], r[2], r[3]);
+    if (two_groups) ldsm_x4_trans(a_hi + col, r[4], r[5], r[6], r[7]);
+    const int j = lane >> 2, q4 = lane & 3;
+    if (!((bits >> j) & 1u)) return;
+    const int rl = w_mb[w] + __popc(mw & ((1u << (shift + j)) - 1u));
+    unsigned char *dst = stage + (size_t)rl * (2 * X);
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        if (g >= 4 && !two_groups) break;
+        const int x = 8 * g + 2 * q4;
+        if (x >= X) continue;
+        if (x + 1 < X && !(X & 1)) {
+            *reinterpret_cast<uint32_t *>(dst + 2 * x) = r[g];
+        } else {
+            *reinterpret_cast<uint16_t *>(dst + 2 * x) = (uint16_t)(r[g] & 0xffffu);
+            if (x + 1 < X) *reinterpret_cast<uint16_t *>(dst + 2 * x + 2) = (uint16_t)(r[g] >> 16);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------- pool rows to global
+// Rows [excl.m, excl.m + agg.m) from the stage area (a group of nthr threads,
+// id gt).  The body goes out in aligned 16-byte stores; the head and tail
+// (< 16 bytes each, shared with neighbouring tiles' rows) in 2-byte stores.
+__device__ __forceinline__ void copy_out(const KArgs &a, const unsigned char *stage, const Agg &excl,
+                                         const Agg &agg, int gt, int nthr)
+{
+    const long long rb = 2ll * a.n_xtal;
+    const long long cap_b = a.pool_cap * rb;
+    const long long gs = excl.m * rb;
+    long long ge = gs + agg.m * rb;
+    if (ge > cap_b) {
+        ge = cap_b;
+        if (gt == 0) set_status_bit(a, DAQ_DEV_POOL_OVERFLOW);
+    }
+    if (ge <= gs) return;
+    unsigned char *g = reinterpret_cast<unsigned char *>(a.pool);
+    long long a16 = (gs + 15) & ~15ll, b16 = ge & ~15ll;
+    if (a16 > ge) a16 = ge;
+    if (b16 < a16) b16 = a16;
+    const int n_head = (int)((a16 - gs) >> 1), n_tail = (int)((ge - b16) >> 1);
+    if (gt < n_head)
+        *reinterpret_cast<uint16_t *>(g + gs + 2 * gt) = *reinterpret_cast<const uint16_t *>(stage + 2 * gt);
+    else if (gt >= 8 && gt < 8 + n_tail) {
+        const long long o = b16 + 2 * (gt - 8);
+        *reinterpret_cast<uint16_t *>(g + o) = *reinterpret_cast<const uint16_t *>(stage + (o - gs));
+    }
+    const int e = (int)(a16 - gs);  // stage offset of global a16: even, < 16
+    const long long n_chunks = (b16 - a16) >> 4;
+    const int o = e >> 2;
+    const bool half = (e & 2) != 0;
+    for (long long i = gt; i < n_chunks; i += nthr) {
+        const uint4 w0 = *reinterpret_cast<const uint4 *>(stage + 16 * i);
+        uint32_t out0, out1, out2, out3;
+        if (e == 0) {
+            out0 = w0.x;
+            out1 = w0.y;
+            out2 = w0.z;
+            out3 = w0.w;
+        } else {
+            const uint4 w1 = *reinterpret_cast<const uint4 *>(stage + 16 * i + 16);
+            uint32_t s0, s1, s2, s3, s4;
+            switch (o) {
+            case 0: s0 = w0.x; s1 = w0.y; s2 = w0.z; s3 = w0.w; s4 = w1.x; break;
+            case 1: s0 = w0.y; s1 = w0.z; s2 = w0.w; s3 = w1.x; s4 = w1.y; break;
+            case 2: s0 = w0.z; s1 = w0.w; s2 = w1.x; s3 = w1.y; s4 = w1.z; break;
+            default: s0 = w0.w; s1 = w1.x; s2 = w1.y; s3 = w1.z; s4 = w1.w; break;
+            }
+            if (half) {
+                out0 = __funnelshift_r(s0, s1, 16);
+                out1 = __funnelshift_r(s1, s2, 16);
+                out2 = __funnelshift_r(s2, s3, 16);
+                out3 = __funnelshift_r(s3, s4, 16);
+            } else {
+                out0 = s0;
+                out1 = s1;
+                out2 = s2;
+                out3 = s3;
+            }
+        }
+        st_global_cs_v4(g + a16 + 16 * i, out0, out1, out2, out3);
+    }
+}
+
+// --------------------------------------------------------------------------- island records (one warp)
+// One record per island end inside the tile.  An island that began in an
+// earlier tile starts at t0 - excl.tr (the marked run entering the tile).
+template <int TW>
+__device__ __forceinline__ void write_headers(const KArgs &a, const TileInfo &T, TileWords w, const Agg &excl,
+                                              int lane)
+{
+    constexpr int NWT = TW / 32;
+    if (lane >= NWT) return;
+    uint32_t E = w.e[lane];
+    const uint32_t Mt = w.m[lane], St = w.s[lane];
+    bool over = false;
+    while (E) {
+        const int b = __ffs(E) - 1;
+        E &= E - 1u;
+        const uint32_t upto = b == 31 ? 0xffffffffu : ((2u << b) - 1u);
+        const uint32_t su = St & upto;
+        const long long idx = excl.s + w.sb[lane] + __popc(su) - 1;
+        const int lrel = su ? 32 * lane + 31 - __clz(su) : w.ls[lane];
+        const long long start = lrel >= 0 ? T.t0 + lrel : T.t0 - excl.tr;
+        const long long t_e = T.t0 + 32 * lane + b;
+        const long long ilen = t_e - start + 1;
+        const long long row_end = excl.m + w.mb[lane] + __popc(Mt & upto) - 1;
+        if (idx < a.hdr_cap) {
+            daq_island *h = a.hdr + idx;
+            h->fill = a.fill_base + T.f;
+            h->calo = T.c;
+            h->start = (int32_t)start;
+            h->len = (int32_t)ilen;
+            h->pool_row = row_end - ilen + 1;
+        } else {
+            over = true;
+        }
+    }
+    if (over) set_status_bit(a, DAQ_DEV_HDR_OVERFLOW);
+}
+
+// --------------------------------------------------------------------------- Q decimation + fill sum
+// Partial bins of the tile (a group of nthr threads): B_D[k] restricted to the
+// tile, added atomically to the calorimeter's int64 histogram.
+__device__ __forceinline__ void q_partial(const KArgs &a, const TileInfo &T, const int32_t *blocksum,
+                                          const int32_t *sarr, int gt, int nthr)
+{
+    for (int d = 0; d < a.n_decim; ++d) {
+        const long long D = a.decim[d];
+        unsigned long long *qrow =
+            reinterpret_cast<unsigned long long *>(a.q + a.qoff[d] + (long long)T.c * a.qbins[d]);
+        const long long k_lo = T.t0 / D, k_hi = (T.t_end - 1) / D;
+        for (long long k = k_lo + gt; k <= k_hi; k += nthr) {
+            const long long lo = (k * D > T.t0 ? k * D : T.t0) - T.t0;
+            const long long hi = (k * D + D < T.t_end ? k * D + D : T.t_end) - T.t0;
+            long long sum = 0;
+            if ((D & 7) == 0) {
+                for (long long b = lo >> 3; b < (hi + 7) >> 3; ++b) sum += blocksum[b];
+            } else {
+                for (long long t = lo; t < hi; ++t) sum += sarr[t];
+            }
+            atomicAdd(qrow + k, (unsigned long long)sum);
+        }
+    }
+}
+
+// Counts of the whole call, from the last tile's inclusive prefix.
+__device__ __forceinline__ void write_counts(const KArgs &a, long long tile, const Agg &incl)
+{
+    a.counts[0] = incl.s;
+    a.counts[1] = incl.m;
+    a.counts[3] = tile + 1;
+    if (!(a.flags & DAQ_SKIP_ISLANDS)) {
+        if (incl.m > a.pool_cap) set_status_bit(a, DAQ_DEV_POOL_OVERFLOW);
+        if (incl.s > a.hdr_cap) set_status_bit(a, DAQ_DEV_HDR_OVERFLOW);
+    }
+}
+
+}  // namespace daq
