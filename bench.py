@@ -277,7 +277,7 @@ def bench_gb300(args, ws, rank, local):
                                f"({raw_bytes / 1e9:.4f} GB), literal noise sigma 3/crystal, T=30, pre=8, post=24, D=32",
                    "fills_per_step_per_gpu": 1, "raw_bytes_per_step_per_gpu": raw_bytes,
                    "l2": "inputs larger than L2 (1.45 GB per step vs 129 MB)", "parallelism": f"replicas x{ws}",
-                   "tile": 448, "grid": "persistent"},
+                   "tile": 448, "grid": "pipelined persistent kernel, one CTA per SM"},
         "pct_of_hbm_peak": round(100.0 * value / ws / peak, 2),
         "pct_of_nominal_hbm": round(100.0 * value / ws / NOMINAL_HBM_GBS, 2),
         "latency_ms": {"p50": round(statistics.median(step_ms), 4),
