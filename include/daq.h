@@ -83,8 +83,9 @@ typedef struct daq_island {
  *                NULL for n_samples each.  Out-of-range values are clamped and
  *                flagged with DAQ_DEV_BAD_FILL_LEN.
  *   flags        DAQ_SKIP_Q | DAQ_SKIP_ISLANDS | DAQ_SYNC.
- *   tile         samples per tile: 0 = default (448, or the largest of 224 and
- *                128 whose shared-memory plan fits); else 128, 224, 448 or 960.
+ *   tile         largest samples per tile to use: 0 = 448; else 128, 224, 448 or
+ *                960.  The call takes the largest supported width not above it
+ *                whose shared-memory plan fits (960 only for the plain kernel).
  *   grid         0  = pipelined persistent kernel, one CTA per SM (default);
  *                > 0 = pipelined kernel with exactly this many CTAs;
  *                -1 = plain kernel, one CTA per tile (non-persistent form);
@@ -96,6 +97,9 @@ typedef struct daq_island {
  *   events       NULL, or a host array of three cudaEvent_t that the call
  *                records on `stream` before the pedestal kernel, between the
  *                two kernels and after the tile kernel (per-kernel timing).
+ *   trace        NULL, or device uint64[max_tiles][DAQ_TRACE_WORDS] (max_tiles
+ *                from daq_trace_tiles()): per-tile %globaltimer stamps of each
+ *                stage (profiling only; costs a few stores per tile).
  */
 typedef struct daq_params {
     int32_t threshold;
@@ -114,7 +118,14 @@ typedef struct daq_params {
     void *workspace;
     size_t workspace_bytes;
     void *const *events;
+    uint64_t *trace;
 } daq_params;
+
+/* Per-tile trace record: stamps in nanoseconds (%globaltimer), 0 = stage not reached.
+ * [0] ticket taken  [1] load issued  [2] load landed  [3] sums done  [4] marks done
+ * [5] look-back start  [6] prefix known  [7] rows staged  [8] writer start
+ * [9] rows written  [10] SM id  [11] tile width  [12..15] reserved */
+#define DAQ_TRACE_WORDS 16
 
 /*
  * Outputs (all device pointers, caller-owned).
@@ -206,6 +217,10 @@ typedef struct daq_host_io {
  */
 int daq_process_fills_host(int n_calo, int n_xtal, int64_t n_samples, int n_fills, const daq_params *params,
                            const daq_islands *islands_dev, int64_t *qhist_inout, const daq_host_io *io);
+
+/* Upper bound on the tiles of a call with these sizes and parameters (rows of
+ * the trace buffer); 0 on invalid arguments. */
+int64_t daq_trace_tiles(int n_calo, int n_xtal, int64_t n_samples, int n_fills, const daq_params *params);
 
 /* Map a host copy of counts[4] to a daq_status (DAQ_OK if no bit is set). */
 int daq_status_from_counts(const int64_t *counts_host);

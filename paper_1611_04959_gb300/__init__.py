@@ -32,7 +32,7 @@ class DaqParams(ctypes.Structure):
                 ("fill_base", ctypes.c_int32), ("fill_len", ctypes.c_void_p), ("flags", ctypes.c_uint32),
                 ("tile", ctypes.c_int32), ("grid", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t), ("events", ctypes.c_void_p)]
+                ("workspace_bytes", ctypes.c_size_t), ("events", ctypes.c_void_p), ("trace", ctypes.c_void_p)]
 
 
 class DaqIslands(ctypes.Structure):
@@ -78,6 +78,8 @@ def lib():
             L.daq_process_fills_host.argtypes = [i32, i32, i64, i32, ctypes.POINTER(DaqParams),
                                                  ctypes.POINTER(DaqIslands), vp, ctypes.POINTER(DaqHostIO)]
             L.daq_process_fills_host.restype = i32
+            L.daq_trace_tiles.argtypes = [i32, i32, i64, i32, ctypes.POINTER(DaqParams)]
+            L.daq_trace_tiles.restype = i64
             L.daq_status_from_counts.argtypes = [vp]
             L.daq_status_from_counts.restype = i32
             L.daq_strerror.argtypes = [i32]
@@ -105,6 +107,15 @@ def daq_workspace_size(n_calo: int, n_xtal: int, n_samples: int, n_fills: int, p
     if rc:
         raise DaqError(rc, "daq_workspace_size")
     return int(out.value)
+
+
+def daq_trace_tiles(n_calo: int, n_xtal: int, n_samples: int, n_fills: int, params: DaqParams) -> int:
+    return int(lib().daq_trace_tiles(n_calo, n_xtal, n_samples, n_fills, ctypes.byref(params)))
+
+
+DAQ_TRACE_WORDS = 16
+TRACE_STAGES = ["ticket", "load_issued", "load_landed", "sums_done", "marks_done", "lookback_start",
+                "prefix_known", "rows_staged", "writer_start", "rows_written", "sm", "tile_width"]
 
 
 def daq_q_bins(n_samples: int, decim: int) -> int:

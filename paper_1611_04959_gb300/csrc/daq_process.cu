@@ -251,6 +251,11 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(KArgs a)
         __syncthreads();
         const TileInfo T = *tinfo;
         if (T.tile < 0) break;
+        if (tid == 0) {
+            trace_stamp(a, T.tile, 0);
+            trace_value(a, T.tile, 10, sm_id());
+            trace_value(a, T.tile, 11, TW);
+        }
 
         if (a.bulk_ok) {
             if (warp == 0) {
@@ -258,6 +263,7 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(KArgs a)
                 if (lane == 0) mbar_arrive_expect_tx(bar, tile_load_bytes(a, T));
                 __syncwarp();
                 issue_tile_load(a, T, tbuf, bar, lane);
+                if (lane == 0) trace_stamp(a, T.tile, 1);
             }
             const bool ok = mbar_wait_bounded(bar, phase, kWaitLimitNs);
             phase ^= 1u;
@@ -271,12 +277,18 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(KArgs a)
             __syncthreads();
         }
 
+        if (tid == 0) trace_stamp(a, T.tile, 2);
         for (int b = warp; b < NB; b += kWarps)
             sum_block(a, T, a_lo, a_hi, two_groups, b, NBT, abyte, blocksum, sarr, lane);
         __syncthreads();
+        if (tid == 0) trace_stamp(a, T.tile, 3);
 
         if (warp == 0) {
             const Agg agg = tile_bits<TW>(a, T, abyte, W, lane);
+            if (lane == 0) {
+                trace_stamp(a, T.tile, 4);
+                trace_stamp(a, T.tile, 5);
+            }
             __syncwarp();
             asm volatile("bar.arrive 1, %0;" ::"r"(kThreads) : "memory");
             Agg excl = agg_identity();
@@ -288,6 +300,7 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(KArgs a)
                 publish(a.status, T.tile, true, combine(excl, agg));
                 s_agg[0] = agg;
                 s_agg[1] = excl;
+                trace_stamp(a, T.tile, 6);
             }
         } else {
             if (!(a.flags & DAQ_SKIP_Q)) q_partial(a, T, blocksum, sarr, tid - 32, kThreads - 32);
@@ -299,10 +312,15 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(KArgs a)
         __syncthreads();
 
         const Agg agg = s_agg[0], excl = s_agg[1];
+        if (tid == 0) {
+            trace_stamp(a, T.tile, 7);
+            trace_stamp(a, T.tile, 8);
+        }
         if (!excl.poison && !(a.flags & DAQ_SKIP_ISLANDS)) {
             copy_out(a, stage, excl, agg, tid, kThreads);
             if (warp == 0) write_headers<TW>(a, T, W, excl, lane);
         }
+        if (tid == 0) trace_stamp(a, T.tile, 9);
         if (tid == 0 && T.tile == total - 1) write_counts(a, T.tile, combine(excl, agg));
     }
 }
@@ -449,12 +467,18 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
                 break;
             }
             const TileInfo T = M->T;
+            if (lane == 0) {
+                trace_stamp(a, T.tile, 0);
+                trace_value(a, T.tile, 10, sm_id());
+                trace_value(a, T.tile, 11, TW);
+            }
             unsigned char *slot = in0 + (size_t)s * X * RS;
             if (a.bulk_ok) {
                 fence_proxy_async_smem();
                 if (lane == 0) mbar_arrive_expect_tx(bars + kBarInFull + s, tile_load_bytes(a, T));
                 __syncwarp();
                 issue_tile_load(a, T, slot, bars + kBarInFull + s, lane);
+                if (lane == 0) trace_stamp(a, T.tile, 1);
                 pending |= 1u << s;
                 pend_parity = (pend_parity & ~(1u << s)) | ((uint32_t)((i / kNIn) & 1) << s);
             } else {
@@ -481,6 +505,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
                 if (lane == 0) mbar_arrive(bars + kBarBits + m);
                 break;
             }
+            if (cw == 0 && lane == 0) trace_stamp(a, T.tile, 2);
             const uint32_t slot_s = smem_addr(in0 + (size_t)s * X * RS);
             const uint32_t a_lo = lane < X ? slot_s + (uint32_t)(lane * RS) : zrow_s;
             const uint32_t a_hi = lane + 32 < X ? slot_s + (uint32_t)((lane + 32) * RS) : zrow_s;
@@ -488,6 +513,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
                 sum_block(a, T, a_lo, a_hi, two_groups, b, NBT, M->abyte, M->blocksum, sarr(m), lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(bars + kBarBits + m);
+            if (cw == 0 && lane == 0) trace_stamp(a, T.tile, 3);
             if (!pipe_wait(a, bars + kBarWords + m, (uint32_t)((i / kNMeta) & 1))) break;
             if (i >= kNOut && !pipe_wait(a, bars + kBarOutEmpty + o, (uint32_t)((i / kNOut - 1) & 1))) break;
             if (!skip_isl) {
@@ -499,6 +525,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
             if (lane == 0) {
                 mbar_arrive(bars + kBarInEmpty + s);
                 mbar_arrive(bars + kBarOutFull + o);
+                if (cw == 0) trace_stamp(a, T.tile, 7);
             }
         }
     } else if (warp == kPipeBits) {
@@ -517,6 +544,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
             }
             const Agg agg = tile_bits<TW>(a, T, M->abyte, words(m), lane);
             if (lane == 0) {
+                trace_stamp(a, T.tile, 4);
                 M->agg = agg;
                 if (T.tile > 0) publish(a.status, T.tile, false, agg);
             }
@@ -538,10 +566,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
                 break;
             }
             const Agg agg = M->agg;
+            if (lane == 0) trace_stamp(a, T.tile, 5);
             const Agg excl = T.tile > 0 ? look_back(a, T.tile, lane) : agg_identity();
             if (lane == 0) {
                 publish(a.status, T.tile, true, combine(excl, agg));
                 M->excl = excl;
+                trace_stamp(a, T.tile, 6);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(bars + kBarExcl + m);
@@ -557,6 +587,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
             const TileInfo T = M->T;
             if (T.tile < 0) break;
             const Agg agg = M->agg, excl = M->excl;
+            if (gt == 0) trace_stamp(a, T.tile, 8);
             if (!(a.flags & DAQ_SKIP_Q)) q_partial(a, T, M->blocksum, sarr(m), gt, nthr);
             if (!pipe_wait(a, bars + kBarOutFull + o, (uint32_t)((i / kNOut) & 1))) break;
             if (!excl.poison && !skip_isl) {
@@ -568,6 +599,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
             if (lane == 0) {
                 mbar_arrive(bars + kBarOutEmpty + o);
                 mbar_arrive(bars + kBarMetaFree + m);
+                if (gt == 0) trace_stamp(a, T.tile, 9);
             }
         }
     }
@@ -652,17 +684,18 @@ static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, con
     if (p->tile != 0 && p->tile != 128 && p->tile != 224 && p->tile != 448 && p->tile != 960) return DAQ_EINVAL;
     pl->pipelined = p->grid >= 0;
     const int hl = (p->post + 1 + 7) & ~7, hr = (p->pre + 1 + 7) & ~7;
+    const int limit = p->tile ? p->tile : 448;
     int chosen = -1;
-    for (int tw : {448, 224, 128, 960}) {
-        if (p->tile != 0 && tw != p->tile) continue;
-        if (p->tile == 0 && tw == 960) continue;
+    for (int tw : {960, 448, 224, 128}) {
+        if (tw > limit) continue;
+        if (tw == 960 && pl->pipelined) continue;
         if (tw + hl + hr > kMaxExtBits) continue;
         plan_geometry(pl, tw, p->pre, p->post, n_xtal);
         if (pl->smem > (size_t)kSmemBudget) continue;
         chosen = tw;
         break;
     }
-    if (chosen < 0) return p->tile ? DAQ_EINVAL : DAQ_EUNSUPPORTED;
+    if (chosen < 0) return DAQ_EUNSUPPORTED;
     pl->max_tiles = (int64_t)n_fills * n_calo * ((n_samples + chosen - 1) / chosen);
     return DAQ_OK;
 }
@@ -809,6 +842,7 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
     a.lens = reinterpret_cast<int32_t *>(ws + wl.lens);
     a.ptot = reinterpret_cast<int32_t *>(ws + wl.ptot);
     a.status = reinterpret_cast<TileStatus *>(ws + wl.status);
+    a.trace = reinterpret_cast<unsigned long long *>(p.trace);
 
     cudaStream_t s = static_cast<cudaStream_t>(p.stream);
     int dev = 0;
@@ -855,6 +889,13 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
         return daq_status_from_counts(h);
     }
     return DAQ_OK;
+}
+
+int64_t daq_trace_tiles(int n_calo, int n_xtal, int64_t n_samples, int n_fills, const daq_params *params)
+{
+    Plan pl;
+    if (make_plan(n_calo, n_xtal, n_samples, n_fills, params, &pl) != DAQ_OK) return 0;
+    return pl.max_tiles;
 }
 
 int daq_status_from_counts(const int64_t *c)

@@ -99,7 +99,25 @@ struct KArgs {
     int32_t *lens;               // [n_fills], clamped
     int32_t *ptot;               // [n_fills * n_calo]
     TileStatus *status;          // [max_tiles]
+    unsigned long long *trace;   // NULL or [max_tiles][16] stage stamps
 };
+
+__device__ __forceinline__ void trace_stamp(const KArgs &a, long long tile, int k)
+{
+    if (a.trace) a.trace[tile * 16 + k] = global_ns();
+}
+
+__device__ __forceinline__ void trace_value(const KArgs &a, long long tile, int k, unsigned long long v)
+{
+    if (a.trace) a.trace[tile * 16 + k] = v;
+}
+
+__device__ __forceinline__ unsigned sm_id()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
 
 struct TileInfo {
     long long tile;  // -1: no more tiles
