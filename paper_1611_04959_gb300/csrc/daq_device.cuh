@@ -117,6 +117,23 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
     return v;
 }
 
+// 128-bit loads and stores of one 16-byte status word (two 64-bit halves).
+__device__ __forceinline__ void ld_acquire_b128(const void *p, unsigned long long &lo, unsigned long long &hi)
+{
+    asm volatile(
+        "{\n\t.reg .b128 t;\n\tld.acquire.gpu.global.b128 t, [%2];\n\tmov.b128 {%0, %1}, t;\n\t}"
+        : "=l"(lo), "=l"(hi)
+        : "l"(p)
+        : "memory");
+}
+
+__device__ __forceinline__ void st_release_b128(void *p, unsigned long long lo, unsigned long long hi)
+{
+    asm volatile("{\n\t.reg .b128 t;\n\tmov.b128 t, {%0, %1};\n\tst.release.gpu.global.b128 [%2], t;\n\t}" ::"l"(lo),
+                 "l"(hi), "l"(p)
+                 : "memory");
+}
+
 // Streaming 16-byte store (output is written once and not re-read here).
 __device__ __forceinline__ void st_global_cs_v4(void *p, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
 {

@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(KArgs a)
     for (;;) {
         if (tid == 0) {
             const long long tk = (long long)atomicAdd(a.ticket, 1u);
-            decode_tile<TW>(a, tk, *tinfo);
+            decode_tile<TW>(a, tk, *tinfo, a.fill_tile_start, a.lens);
         }
         __syncthreads();
         const TileInfo T = *tinfo;
@@ -278,8 +278,9 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(KArgs a)
         }
 
         if (tid == 0) trace_stamp(a, T.tile, 2);
-        for (int b = warp; b < NB; b += kWarps)
-            sum_block(a, T, a_lo, a_hi, two_groups, b, NBT, abyte, blocksum, sarr, lane);
+        for (int b = warp; b < NB; b += 2 * kWarps)
+            sum_block2(a, T, a_lo, a_hi, two_groups, b, b + kWarps < NB ? b + kWarps : -1, NBT, abyte, blocksum,
+                       sarr, lane);
         __syncthreads();
         if (tid == 0) trace_stamp(a, T.tile, 3);
 
@@ -331,14 +332,16 @@ constexpr int kPipeProducer = 0;           // tickets, decode, bulk loads
 constexpr int kPipeCompute0 = 1;           // crystal sums, threshold bits, staging
 constexpr int kPipeNCompute = 8;
 constexpr int kPipeBits = kPipeCompute0 + kPipeNCompute;  // windows, merge, aggregate
-constexpr int kPipeLook = kPipeBits + 1;                  // decoupled look-back
-constexpr int kPipeWriter0 = kPipeLook + 1;               // Q, pool rows, island records
+constexpr int kPipeLook = kPipeBits + 1;                  // decoupled look-back (alternate tiles)
+constexpr int kPipeNLook = 2;
+constexpr int kPipeWriter0 = kPipeLook + kPipeNLook;      // Q, pool rows, island records
 constexpr int kPipeNWriter = 4;
 constexpr int kPipeWarps = kPipeWriter0 + kPipeNWriter;
 constexpr int kPipeThreads = 32 * kPipeWarps;
 constexpr int kNIn = 2;   // input tile slots
 constexpr int kNOut = 2;  // stage slots
 constexpr int kNMeta = 4; // tiles in flight per CTA
+constexpr int kPlanCache = 64;  // fills whose tile plan is cached in shared memory
 
 template <int TW> struct PipeMeta {
     TileInfo T;
@@ -392,6 +395,8 @@ template <int TW> static size_t pipe_smem_bytes(int X, int rs, int need_sarr)
     b += (size_t)kNMeta * ((sizeof(PipeMeta<TW>) + 15) & ~size_t(15));
     b += need_sarr ? (size_t)kNMeta * TW * 4 : 0;
     b += (size_t)kNBars * 8 + 16;
+    b += (size_t)(kPlanCache + 1) * 8 + (size_t)kPlanCache * 4 + 16;
+    b += 16;  // end index
     return (b + 127) & ~size_t(127);
 }
 
@@ -413,6 +418,19 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
     int32_t *sarr0 = reinterpret_cast<int32_t *>(meta0 + kNMeta * meta_bytes);
     uint64_t *bars = reinterpret_cast<uint64_t *>(
         (reinterpret_cast<uintptr_t>(sarr0 + (a.need_sarr ? kNMeta * TW : 0)) + 15) & ~uintptr_t(15));
+    long long *plan_fts = reinterpret_cast<long long *>(bars + kNBars);
+    int32_t *plan_lens = reinterpret_cast<int32_t *>(plan_fts + kPlanCache + 1);
+    // iteration at which the producer found no more tiles (read by the look-back warps)
+    volatile long long *s_end = reinterpret_cast<volatile long long *>(
+        (reinterpret_cast<uintptr_t>(plan_lens + kPlanCache) + 15) & ~uintptr_t(15));
+    if (tid == 0) *s_end = 0x7fffffffffffffffll;
+    const bool cached = a.n_fills <= kPlanCache;
+    if (cached) {
+        for (int f = tid; f <= a.n_fills; f += kPipeThreads) plan_fts[f] = a.fill_tile_start[f];
+        for (int f = tid; f < a.n_fills; f += kPipeThreads) plan_lens[f] = a.lens[f];
+    }
+    const long long *fts = cached ? plan_fts : a.fill_tile_start;
+    const int32_t *lens = cached ? plan_lens : a.lens;
     auto meta = [&](int m) { return reinterpret_cast<PipeMeta<TW> *>(meta0 + m * meta_bytes); };
     auto sarr = [&](int m) { return sarr0 + (a.need_sarr ? m * TW : 0); };
     auto words = [&](int m) {
@@ -458,12 +476,15 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
             int valid = 0;
             if (lane == 0) {
                 const long long tk = (long long)atomicAdd(a.ticket, 1u);
-                valid = decode_tile<TW>(a, tk, M->T);
+                valid = decode_tile<TW>(a, tk, M->T, fts, lens);
             }
             valid = __shfl_sync(kFull, valid, 0);
             __syncwarp();
             if (!valid) {
-                if (lane == 0) mbar_arrive(bars + kBarInFull + s);
+                if (lane == 0) {
+                    *s_end = i;
+                    mbar_arrive(bars + kBarInFull + s);
+                }
                 break;
             }
             const TileInfo T = M->T;
@@ -509,8 +530,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
             const uint32_t slot_s = smem_addr(in0 + (size_t)s * X * RS);
             const uint32_t a_lo = lane < X ? slot_s + (uint32_t)(lane * RS) : zrow_s;
             const uint32_t a_hi = lane + 32 < X ? slot_s + (uint32_t)((lane + 32) * RS) : zrow_s;
-            for (int b = cw; b < NB; b += kPipeNCompute)
-                sum_block(a, T, a_lo, a_hi, two_groups, b, NBT, M->abyte, M->blocksum, sarr(m), lane);
+            for (int b = cw; b < NB; b += 2 * kPipeNCompute)
+                sum_block2(a, T, a_lo, a_hi, two_groups, b, b + kPipeNCompute < NB ? b + kPipeNCompute : -1, NBT,
+                           M->abyte, M->blocksum, sarr(m), lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(bars + kBarBits + m);
             if (cw == 0 && lane == 0) trace_stamp(a, T.tile, 3);
@@ -554,11 +576,26 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
                 mbar_arrive(bars + kBarAgg + m);
             }
         }
-    } else if (warp == kPipeLook) {
+    } else if (warp >= kPipeLook && warp < kPipeLook + kPipeNLook) {
         // ------------------------------------------------------------ decoupled look-back
-        for (long long i = 0;; ++i) {
+        for (long long i = warp - kPipeLook;; i += kPipeNLook) {
             const int m = (int)(i % kNMeta);
-            if (!pipe_wait(a, bars + kBarAgg + m, (uint32_t)((i / kNMeta) & 1))) break;
+            // the other look-back warp may own the end marker: stop once it is past
+            bool ready = false, done = false;
+            const uint64_t t0 = global_ns();
+            for (uint32_t k = 0; !ready && !done; ++k) {
+                ready = mbar_try_wait(bars + kBarAgg + m, (uint32_t)((i / kNMeta) & 1));
+                if (!ready && *s_end < i) done = true;
+                if (!ready && (k & 15u) == 15u) {
+                    if (global_ns() - t0 > kWaitLimitNs) {
+                        set_status_bit(a, DAQ_DEV_TIMEOUT);
+                        done = true;
+                    } else if (aborted(a)) {
+                        done = true;
+                    }
+                }
+            }
+            if (!ready) break;
             PipeMeta<TW> *M = meta(m);
             const TileInfo T = M->T;
             if (T.tile < 0) {
@@ -675,7 +712,9 @@ static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, con
     if (p->pre < 0 || p->post < 0 || p->pre + p->post > 512 || p->ped_samples < 1) return DAQ_EINVAL;
     if (p->n_decim < 0 || p->n_decim > 2) return DAQ_EINVAL;
     if (p->grid < -2) return DAQ_EINVAL;
-    if (n_samples > (int64_t)INT32_MAX) return DAQ_EUNSUPPORTED;
+    // scan fields: trailing run < 2^30 samples, island count < 2^31
+    if (n_samples > ((int64_t)1 << 30) || (int64_t)n_fills * n_calo * n_samples > ((int64_t)1 << 32))
+        return DAQ_EUNSUPPORTED;
     pl->need_sarr = 0;
     for (int d = 0; d < p->n_decim; ++d) {
         if (p->decim[d] < 1) return DAQ_EINVAL;

@@ -19,13 +19,17 @@ constexpr uint64_t kWaitLimitNs = 4000000000ull;  // bounded device waits (4 s)
 constexpr int kMaxXtal = 64;
 constexpr int kMaxExtBits = 1024;  // tile + halos: one warp of 32-bit words
 
-// Scan state of one tile: aggregate and inclusive prefix, each a (flag, payload) pair.
-// flag word  = (marked samples << 2) | kind, kind 1 = valid, 2 = poisoned
-// payload    = (island starts << 32) | (trailing run << 1) | continues
-struct TileStatus {
-    unsigned long long agg_payload, agg_flag;
-    unsigned long long inc_payload, inc_flag;
+// Scan state of one tile: one 16-byte word, written whole (128-bit release
+// store) first with the tile's aggregate, later with its inclusive prefix, and
+// read whole (128-bit acquire load).
+//   lo = (marked samples << 2) | kind
+//   hi = (island starts << 33) | (trailing run << 3) | (continues << 2) | kind
+// kind: 0 nothing yet, 1 aggregate, 2 inclusive prefix, 3 poisoned prefix.  The
+// kind is kept in both halves; a read whose halves disagree is not used.
+struct __align__(16) TileStatus {
+    unsigned long long lo, hi;
 };
+constexpr unsigned kKindAgg = 1, kKindInc = 2, kKindPoison = 3;
 
 struct Agg {
     long long m;   // marked samples (pool rows)
@@ -145,19 +149,20 @@ __device__ __forceinline__ bool aborted(const KArgs &a)
 // Map a ticket to its tile.  Tiles are numbered fill by fill, calorimeter by
 // calorimeter, then in time; a fill of length len has ceil(len / TW) tiles
 // per calorimeter.
-template <int TW> __device__ bool decode_tile(const KArgs &a, long long tile, TileInfo &T)
+template <int TW>
+__device__ bool decode_tile(const KArgs &a, long long tile, TileInfo &T, const long long *fts, const int32_t *lens)
 {
-    const long long total = a.fill_tile_start[a.n_fills];
+    const long long total = fts[a.n_fills];
     T.tile = -1;
     if (tile >= total) return false;
     int lo = 0, hi = a.n_fills - 1;  // last fill whose first tile <= tile
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (a.fill_tile_start[mid] <= tile) lo = mid; else hi = mid - 1;
+        if (fts[mid] <= tile) lo = mid; else hi = mid - 1;
     }
-    const long long len = a.lens[lo];
+    const long long len = lens[lo];
     const long long tpc = (len + TW - 1) / TW;
-    const long long rem = tile - a.fill_tile_start[lo];
+    const long long rem = tile - fts[lo];
     T.tile = tile;
     T.f = lo;
     T.c = (int)(rem / tpc);
@@ -209,6 +214,55 @@ __device__ __forceinline__ void sum_block(const KArgs &a, const TileInfo &T, uin
         sv += __shfl_xor_sync(kFull, sv, 16);
         if (lane == 0) blocksum[bt] = sv;
         if (a.need_sarr && (lane & 3) == 0 && in) sarr[8 * bt + j] = S;
+    }
+}
+
+// Two blocks at once (b1 < 0: only b0): both blocks' shared-memory loads are
+// issued before either is used.
+__device__ __forceinline__ void sum_block2(const KArgs &a, const TileInfo &T, uint32_t a_lo, uint32_t a_hi,
+                                           bool two_groups, int b0, int b1, int nbt, uint8_t *abyte,
+                                           int32_t *blocksum, int32_t *sarr, int lane)
+{
+    uint32_t r[2][8];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r[u][k] = 0u;
+    const uint32_t c0 = 16u * (uint32_t)b0, c1 = 16u * (uint32_t)(b1 >= 0 ? b1 : b0);
+    ldsm_x4_trans(a_lo + c0, r[0][0], r[0][1], r[0][2], r[0][3]);
+    if (two_groups) ldsm_x4_trans(a_hi + c0, r[0][4], r[0][5], r[0][6], r[0][7]);
+    if (b1 >= 0) {
+        ldsm_x4_trans(a_lo + c1, r[1][0], r[1][1], r[1][2], r[1][3]);
+        if (two_groups) ldsm_x4_trans(a_hi + c1, r[1][4], r[1][5], r[1][6], r[1][7]);
+    }
+    const int j = lane >> 2;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int b = u == 0 ? b0 : b1;
+        if (b < 0) break;
+        int acc = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc = __dp2a_lo((int)r[u][k], 0x0101, acc);
+        acc += __shfl_xor_sync(kFull, acc, 1);
+        acc += __shfl_xor_sync(kFull, acc, 2);
+        const long long t = T.t0 - a.hl + 8 * b + j;
+        const int S = acc - T.ptot;
+        const bool cross = (t >= 0) && (t < T.len) && (S > a.threshold);
+        uint32_t v = __ballot_sync(kFull, cross) & 0x11111111u;
+        v = (v | (v >> 3)) & 0x03030303u;
+        v = (v | (v >> 6)) & 0x000f000fu;
+        v = (v | (v >> 12)) & 0xffu;
+        if (lane == 0) abyte[b] = (uint8_t)v;
+        const int bt = b - a.hl / 8;
+        if (bt >= 0 && bt < nbt) {
+            const bool in = t < T.t_end;
+            int sv = in ? S : 0;
+            sv += __shfl_xor_sync(kFull, sv, 4);
+            sv += __shfl_xor_sync(kFull, sv, 8);
+            sv += __shfl_xor_sync(kFull, sv, 16);
+            if (lane == 0) blocksum[bt] = sv;
+            if (a.need_sarr && (lane & 3) == 0 && in) sarr[8 * bt + j] = S;
+        }
     }
 }
 
@@ -286,34 +340,33 @@ __device__ __forceinline__ Agg tile_bits(const KArgs &a, const TileInfo &T, cons
 // --------------------------------------------------------------------------- cross-tile scan
 __device__ __forceinline__ void publish(TileStatus *st, long long tile, bool inclusive, const Agg &v)
 {
-    const unsigned long long flag = ((unsigned long long)v.m << 2) | (v.poison ? 2ull : 1ull);
-    const unsigned long long payload =
-        ((unsigned long long)v.s << 32) | ((unsigned long long)v.tr << 1) | (unsigned long long)(v.full != 0);
-    if (inclusive) {
-        st_relaxed_u64(&st[tile].inc_payload, payload);
-        st_release_u64(&st[tile].inc_flag, flag);
-    } else {
-        st_relaxed_u64(&st[tile].agg_payload, payload);
-        st_release_u64(&st[tile].agg_flag, flag);
-    }
+    const unsigned long long kind = inclusive ? (v.poison ? kKindPoison : kKindInc) : kKindAgg;
+    const unsigned long long lo = ((unsigned long long)v.m << 2) | kind;
+    const unsigned long long hi = ((unsigned long long)v.s << 33) | ((unsigned long long)v.tr << 3) |
+                                  ((unsigned long long)(v.full != 0) << 2) | kind;
+    st_release_b128(&st[tile], lo, hi);
 }
 
-__device__ __forceinline__ Agg decode_status(unsigned long long flag, unsigned long long payload)
+// kind of a status read (0 when not yet published or the halves disagree)
+__device__ __forceinline__ unsigned read_status(const TileStatus *st, long long idx, Agg &v)
 {
-    Agg r;
-    r.m = (long long)(flag >> 2);
-    r.poison = (flag & 3ull) == 2ull;
-    r.s = (long long)(payload >> 32);
-    r.tr = (long long)((payload >> 1) & 0x7fffffffull);
-    r.full = (int)(payload & 1ull);
-    return r;
+    unsigned long long lo, hi;
+    ld_acquire_b128(&st[idx], lo, hi);
+    const unsigned k = (unsigned)(lo & 3ull);
+    if (k == 0 || k != (unsigned)(hi & 3ull)) return 0;
+    v.m = (long long)(lo >> 2);
+    v.s = (long long)(hi >> 33);
+    v.tr = (long long)((hi >> 3) & 0x3fffffffull);
+    v.full = (int)((hi >> 2) & 1ull);
+    v.poison = k == kKindPoison;
+    return k;
 }
 
 // Decoupled look-back (one warp): exclusive prefix of `tile` over all earlier
-// tiles.  Each round reads 128 predecessors (4 per lane), stops at the nearest
-// inclusive prefix, and combines aggregates in order.  Bounded: gives up after
-// kWaitLimitNs or when another CTA has flagged a timeout, returning a poisoned
-// prefix.
+// tiles.  Each round reads 128 predecessors (4 per lane, one 16-byte load
+// each), stops at the nearest inclusive prefix, and combines the aggregates in
+// between in order.  Bounded: gives up after kWaitLimitNs or once another CTA
+// has flagged a timeout, returning a poisoned prefix.
 __device__ Agg look_back(const KArgs &a, long long tile, int lane)
 {
     constexpr int PER = 4;
@@ -323,33 +376,20 @@ __device__ Agg look_back(const KArgs &a, long long tile, int lane)
     uint64_t t_start = 0;
     bool waiting = false;
     for (uint32_t iter = 0;; ++iter) {
-        int kind[PER];
+        unsigned kind[PER];
         Agg v[PER];
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
             const long long idx = pos - (PER * lane + j);
-            kind[j] = 2;
             v[j] = agg_identity();
-            if (idx >= 0) {
-                kind[j] = 0;
-                unsigned long long fl = ld_acquire_u64(&st[idx].inc_flag);
-                if (fl & 3ull) {
-                    kind[j] = 2;
-                    v[j] = decode_status(fl, ld_relaxed_u64(&st[idx].inc_payload));
-                } else {
-                    fl = ld_acquire_u64(&st[idx].agg_flag);
-                    if (fl & 3ull) {
-                        kind[j] = 1;
-                        v[j] = decode_status(fl, ld_relaxed_u64(&st[idx].agg_payload));
-                    }
-                }
-            }
+            kind[j] = kKindInc;
+            if (idx >= 0) kind[j] = read_status(st, idx, v[j]);
         }
         // nearest inclusive prefix g = PER * lane + j
         int first_inc = 1 << 30, first_missing = 1 << 30;
 #pragma unroll
         for (int j = PER - 1; j >= 0; --j) {
-            if (kind[j] == 2) first_inc = PER * lane + j;
+            if (kind[j] >= kKindInc) first_inc = PER * lane + j;
             if (kind[j] == 0) first_missing = PER * lane + j;
         }
         int stop = first_inc, missing = first_missing;
@@ -373,7 +413,6 @@ __device__ Agg look_back(const KArgs &a, long long tile, int lane)
                     return acc;
                 }
             }
-            __nanosleep(32);
             continue;
         }
         // this lane's entries up to last_needed, in order (latest last)
@@ -431,6 +470,25 @@ __device__ __forceinline__ void stage_block(const KArgs &a, uint32_t a_lo, uint3
 }
 
 // --------------------------------------------------------------------------- pool rows to global
+// 16 bytes starting e bytes (even, < 16) into the 32 bytes at p (16-aligned).
+__device__ __forceinline__ uint4 shifted_chunk(const unsigned char *p, int e)
+{
+    const uint4 w0 = *reinterpret_cast<const uint4 *>(p);
+    if (e == 0) return w0;
+    const uint4 w1 = *reinterpret_cast<const uint4 *>(p + 16);
+    uint32_t s0, s1, s2, s3, s4;
+    switch (e >> 2) {
+    case 0: s0 = w0.x; s1 = w0.y; s2 = w0.z; s3 = w0.w; s4 = w1.x; break;
+    case 1: s0 = w0.y; s1 = w0.z; s2 = w0.w; s3 = w1.x; s4 = w1.y; break;
+    case 2: s0 = w0.z; s1 = w0.w; s2 = w1.x; s3 = w1.y; s4 = w1.z; break;
+    default: s0 = w0.w; s1 = w1.x; s2 = w1.y; s3 = w1.z; s4 = w1.w; break;
+    }
+    if (e & 2)
+        return make_uint4(__funnelshift_r(s0, s1, 16), __funnelshift_r(s1, s2, 16), __funnelshift_r(s2, s3, 16),
+                          __funnelshift_r(s3, s4, 16));
+    return make_uint4(s0, s1, s2, s3);
+}
+
 // Rows [excl.m, excl.m + agg.m) from the stage area (a group of nthr threads,
 // id gt).  The body goes out in aligned 16-byte stores; the head and tail
 // (< 16 bytes each, shared with neighbouring tiles' rows) in 2-byte stores.
@@ -459,38 +517,19 @@ __device__ __forceinline__ void copy_out(const KArgs &a, const unsigned char *st
     }
     const int e = (int)(a16 - gs);  // stage offset of global a16: even, < 16
     const long long n_chunks = (b16 - a16) >> 4;
-    const int o = e >> 2;
-    const bool half = (e & 2) != 0;
-    for (long long i = gt; i < n_chunks; i += nthr) {
-        const uint4 w0 = *reinterpret_cast<const uint4 *>(stage + 16 * i);
-        uint32_t out0, out1, out2, out3;
-        if (e == 0) {
-            out0 = w0.x;
-            out1 = w0.y;
-            out2 = w0.z;
-            out3 = w0.w;
-        } else {
-            const uint4 w1 = *reinterpret_cast<const uint4 *>(stage + 16 * i + 16);
-            uint32_t s0, s1, s2, s3, s4;
-            switch (o) {
-            case 0: s0 = w0.x; s1 = w0.y; s2 = w0.z; s3 = w0.w; s4 = w1.x; break;
-            case 1: s0 = w0.y; s1 = w0.z; s2 = w0.w; s3 = w1.x; s4 = w1.y; break;
-            case 2: s0 = w0.z; s1 = w0.w; s2 = w1.x; s3 = w1.y; s4 = w1.z; break;
-            default: s0 = w0.w; s1 = w1.x; s2 = w1.y; s3 = w1.z; s4 = w1.w; break;
-            }
-            if (half) {
-                out0 = __funnelshift_r(s0, s1, 16);
-                out1 = __funnelshift_r(s1, s2, 16);
-                out2 = __funnelshift_r(s2, s3, 16);
-                out3 = __funnelshift_r(s3, s4, 16);
-            } else {
-                out0 = s0;
-                out1 = s1;
-                out2 = s2;
-                out3 = s3;
-            }
+    constexpr int U = 4;  // chunks per thread per round: loads first, then stores
+    for (long long i0 = gt; i0 < n_chunks; i0 += (long long)U * nthr) {
+        uint4 out[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long i = i0 + (long long)u * nthr;
+            if (i < n_chunks) out[u] = shifted_chunk(stage + 16 * i, e);
         }
-        st_global_cs_v4(g + a16 + 16 * i, out0, out1, out2, out3);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long i = i0 + (long long)u * nthr;
+            if (i < n_chunks) st_global_cs_v4(g + a16 + 16 * i, out[u].x, out[u].y, out[u].z, out[u].w);
+        }
     }
 }
 
