@@ -124,7 +124,8 @@ typedef struct daq_params {
 /* Per-tile trace record: stamps in nanoseconds (%globaltimer), 0 = stage not reached.
  * [0] ticket taken  [1] load issued  [2] load landed  [3] sums done  [4] marks done
  * [5] look-back start  [6] prefix known  [7] rows staged  [8] writer start
- * [9] rows written  [10] SM id  [11] tile width  [12..15] reserved */
+ * [9] rows written  [10] SM id  [11] tile width  [12] copy start  [13] copy done
+ * [14] look-back rounds * 100000 + wait polls  [15] input slot free (pipelined kernel) */
 #define DAQ_TRACE_WORDS 16
 
 /*

@@ -115,7 +115,8 @@ def daq_trace_tiles(n_calo: int, n_xtal: int, n_samples: int, n_fills: int, para
 
 DAQ_TRACE_WORDS = 16
 TRACE_STAGES = ["ticket", "load_issued", "load_landed", "sums_done", "marks_done", "lookback_start",
-                "prefix_known", "rows_staged", "writer_start", "rows_written", "sm", "tile_width"]
+                "prefix_known", "rows_staged", "writer_start", "rows_written", "sm", "tile_width",
+                "copy_start", "copy_done", "lookback_rounds_waits", "slot_free"]
 
 
 def daq_q_bins(n_samples: int, decim: int) -> int:

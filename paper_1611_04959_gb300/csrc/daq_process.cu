@@ -474,9 +474,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
             pending &= ~(1u << s);
             PipeMeta<TW> *M = meta(m);
             int valid = 0;
+            const unsigned long long t_free = global_ns();
             if (lane == 0) {
                 const long long tk = (long long)atomicAdd(a.ticket, 1u);
                 valid = decode_tile<TW>(a, tk, M->T, fts, lens);
+                if (valid) trace_value(a, tk, 15, t_free);
             }
             valid = __shfl_sync(kFull, valid, 0);
             __syncwarp();
@@ -604,11 +606,13 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
             }
             const Agg agg = M->agg;
             if (lane == 0) trace_stamp(a, T.tile, 5);
-            const Agg excl = T.tile > 0 ? look_back(a, T.tile, lane) : agg_identity();
+            unsigned lb_stats = 0;
+            const Agg excl = T.tile > 0 ? look_back(a, T.tile, lane, &lb_stats) : agg_identity();
             if (lane == 0) {
                 publish(a.status, T.tile, true, combine(excl, agg));
                 M->excl = excl;
                 trace_stamp(a, T.tile, 6);
+                trace_value(a, T.tile, 14, lb_stats);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(bars + kBarExcl + m);
@@ -627,8 +631,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
             if (gt == 0) trace_stamp(a, T.tile, 8);
             if (!(a.flags & DAQ_SKIP_Q)) q_partial(a, T, M->blocksum, sarr(m), gt, nthr);
             if (!pipe_wait(a, bars + kBarOutFull + o, (uint32_t)((i / kNOut) & 1))) break;
+            if (gt == 0) trace_stamp(a, T.tile, 12);
             if (!excl.poison && !skip_isl) {
                 copy_out(a, out0 + (size_t)o * stage_bytes, excl, agg, gt, nthr);
+                if (gt == 0) trace_stamp(a, T.tile, 13);
                 if (warp == kPipeWriter0) write_headers<TW>(a, T, words(m), excl, lane);
             }
             if (gt == 0 && T.tile == total - 1) write_counts(a, T.tile, combine(excl, agg));

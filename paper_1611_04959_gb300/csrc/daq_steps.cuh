@@ -367,9 +367,10 @@ __device__ __forceinline__ unsigned read_status(const TileStatus *st, long long 
 // each), stops at the nearest inclusive prefix, and combines the aggregates in
 // between in order.  Bounded: gives up after kWaitLimitNs or once another CTA
 // has flagged a timeout, returning a poisoned prefix.
-__device__ Agg look_back(const KArgs &a, long long tile, int lane)
+__device__ Agg look_back(const KArgs &a, long long tile, int lane, unsigned *stats = nullptr)
 {
     constexpr int PER = 4;
+    unsigned rounds = 0, waits = 0;
     const TileStatus *st = a.status;
     long long pos = tile - 1;
     Agg acc = agg_identity();
@@ -401,6 +402,7 @@ __device__ Agg look_back(const KArgs &a, long long tile, int lane)
         const int last_needed = stop < (1 << 30) ? stop : 32 * PER - 1;
         if (missing <= last_needed) {
             // a needed predecessor has published nothing yet: wait (bounded)
+            ++waits;
             if (!waiting) {
                 t_start = global_ns();
                 waiting = true;
@@ -428,7 +430,11 @@ __device__ Agg look_back(const KArgs &a, long long tile, int lane)
         }
         const Agg window = shfl_agg(lane_acc, 0);
         acc = combine(window, acc);
-        if (stop < (1 << 30)) return acc;
+        ++rounds;
+        if (stop < (1 << 30)) {
+            if (stats) *stats = rounds * 100000u + waits;
+            return acc;
+        }
         pos -= 32 * PER;
         waiting = false;
     }

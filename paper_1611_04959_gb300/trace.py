@@ -16,9 +16,10 @@ import numpy as np
 
 from . import DAQ_TRACE_WORDS, TRACE_STAGES
 
-STAGE_PAIRS = [("ticket", "load_issued"), ("load_issued", "load_landed"), ("load_landed", "sums_done"),
+STAGE_PAIRS = [("slot_free", "ticket"), ("ticket", "load_issued"), ("load_issued", "load_landed"), ("load_landed", "sums_done"),
                ("sums_done", "marks_done"), ("marks_done", "lookback_start"), ("lookback_start", "prefix_known"),
                ("marks_done", "rows_staged"), ("prefix_known", "writer_start"), ("rows_staged", "writer_start"),
+               ("writer_start", "copy_start"), ("copy_start", "copy_done"), ("copy_done", "rows_written"),
                ("writer_start", "rows_written"), ("ticket", "rows_written")]
 
 
@@ -31,10 +32,17 @@ def summarize(tr: np.ndarray) -> dict:
     out = {"tiles": int(len(tr)), "span_us": float((tr[:, idx["rows_written"]].max() - t0) / 1e3)}
     stages = {}
     for a, b in STAGE_PAIRS:
+        if not (tr[:, idx[a]] > 0).any() or not (tr[:, idx[b]] > 0).any():
+            continue
         d = (tr[:, idx[b]] - tr[:, idx[a]]) / 1e3
         stages[f"{a}->{b}"] = {"p50_us": round(float(np.median(d)), 3), "p90_us": round(float(np.percentile(d, 90)), 3),
                                "max_us": round(float(d.max()), 3)}
     out["stages"] = stages
+    lb = tr[:, idx["lookback_rounds_waits"]]
+    if lb.any():
+        out["lookback_rounds_p50"] = float(np.median(lb // 100000))
+        out["lookback_wait_polls_p50"] = float(np.median(lb % 100000))
+        out["lookback_wait_polls_p90"] = float(np.percentile(lb % 100000, 90))
     # tiles in flight (ticket .. rows_written) sampled on a time grid
     starts, ends = tr[:, idx["ticket"]] - t0, tr[:, idx["rows_written"]] - t0
     grid = np.linspace(0, ends.max(), 200)
