@@ -117,6 +117,27 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
     return v;
 }
 
+// 2-D tensor TMA load of one box into shared memory; completion counted in
+// bytes on `bar`.  c0 (innermost, in elements) must be a multiple of 8 for
+// 16-bit data; out-of-range coordinates read as zero.
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int c0, int c1, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void ld_relaxed_b128(const void *p, unsigned long long &lo, unsigned long long &hi)
+{
+    asm volatile(
+        "{\n\t.reg .b128 t;\n\tld.relaxed.gpu.global.b128 t, [%2];\n\tmov.b128 {%0, %1}, t;\n\t}"
+        : "=l"(lo), "=l"(hi)
+        : "l"(p)
+        : "memory");
+}
+
 // 128-bit loads and stores of one 16-byte status word (two 64-bit halves).
 __device__ __forceinline__ void ld_acquire_b128(const void *p, unsigned long long &lo, unsigned long long &hi)
 {

@@ -31,6 +31,8 @@
 //
 // Every quantity is an integer, so results do not depend on kernel, tile
 // size, grid size or the order in which tiles run.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -161,51 +163,41 @@ __global__ void __launch_bounds__(kThreads) daq_prepare_kernel(KArgs a, int tw)
     }
 }
 
-// Issue the bulk copies of one tile's rows (one warp; the caller armed `bar`).
+// Issue the TMA box loads of one tile (one thread; the caller armed `bar`).
 __device__ __forceinline__ void issue_tile_load(const KArgs &a, const TileInfo &T, unsigned char *slot,
-                                                uint64_t *bar, int lane)
+                                                uint64_t *bar)
 {
-    const int X = a.n_xtal, RS = a.rs;
-    const long long e0 = T.t0 - a.hl;
-    const long long lo = e0 > 0 ? e0 : 0;
-    const long long hi_want = T.t0 + (long long)a.ew - a.hl;  // t0 + TW + HR
-    const long long hi = hi_want < a.n_samples ? hi_want : a.n_samples;
-    const uint32_t row_bytes = (uint32_t)((hi - lo) * 2);
-    const long long cf = (long long)T.f * a.n_calo + T.c;
-    const int16_t *rows = a.samples + cf * X * a.n_samples;
-    for (int x = lane; x < X; x += 32)
-        bulk_g2s(slot + (size_t)x * RS + (lo - e0) * 2, rows + (long long)x * a.n_samples + lo, row_bytes, bar);
+    const int c0 = (int)(T.t0 - a.hl);
+    const int c1 = (int)(((long long)T.f * a.n_calo + T.c) * a.n_xtal);
+    for (int k = 0; k < a.nbox; ++k) tma_load_2d(slot + (size_t)k * a.box_stride, &a.tmap, c0 + k * a.boxw, c1, bar);
 }
 
-__device__ __forceinline__ uint32_t tile_load_bytes(const KArgs &a, const TileInfo &T)
+__device__ __forceinline__ uint32_t tile_load_bytes(const KArgs &a)
 {
-    const long long e0 = T.t0 - a.hl;
-    const long long lo = e0 > 0 ? e0 : 0;
-    const long long hi_want = T.t0 + (long long)a.ew - a.hl;
-    const long long hi = hi_want < a.n_samples ? hi_want : a.n_samples;
-    return (uint32_t)((hi - lo) * 2) * (uint32_t)a.n_xtal;
+    return (uint32_t)a.nbox * (uint32_t)a.n_xtal * (uint32_t)a.rs;
 }
 
-// Fallback load with plain loads (rows not 16-byte aligned).
+// Fallback load with plain loads (rows not 16-byte aligned), same layout as the boxes.
 __device__ __forceinline__ void plain_tile_load(const KArgs &a, const TileInfo &T, unsigned char *slot, int tid,
                                                 int nthr)
 {
-    const int X = a.n_xtal, EW = a.ew, RS = a.rs;
+    const int X = a.n_xtal, W = a.nbox * a.boxw;
     const long long e0 = T.t0 - a.hl;
     const long long cf = (long long)T.f * a.n_calo + T.c;
     const int16_t *rows = a.samples + cf * X * a.n_samples;
-    for (int i = tid; i < X * EW; i += nthr) {
-        const int x = i / EW, col = i - x * EW;
-        const long long t = e0 + col;
+    for (int i = tid; i < X * W; i += nthr) {
+        const int x = i / W, c = i - x * W;
+        const int k = c / a.boxw, col = c - k * a.boxw;
+        const long long t = e0 + c;
         int16_t v = 0;
         if (t >= 0 && t < a.n_samples) v = rows[(long long)x * a.n_samples + t];
-        reinterpret_cast<int16_t *>(slot + (size_t)x * RS)[col] = v;
+        *reinterpret_cast<int16_t *>(slot + (size_t)k * a.box_stride + (size_t)x * a.rs + 2 * col) = v;
     }
 }
 
 // ============================================================================ plain tile kernel
 template <int TW>
-__global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(KArgs a)
+__global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(const __grid_constant__ KArgs a)
 {
     constexpr int NWT = TW / 32;
     constexpr int NBT = TW / 8;
@@ -214,8 +206,8 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(KArgs a)
     const int X = a.n_xtal, RS = a.rs;
     const int NB = a.ew / 8;
 
-    unsigned char *tbuf = smem;                                    // X rows x RS bytes
-    unsigned char *zrow = tbuf + (size_t)X * RS;                   // zero row
+    unsigned char *tbuf = smem;                                    // tile slot (nbox boxes)
+    unsigned char *zrow = tbuf + a.slot_bytes;                     // zero row
     unsigned char *stage = zrow + RS;                              // TW * 2X + 32 bytes
     const int stage_bytes = ((TW * 2 * X + 32) + 15) & ~15;
     uint8_t *abyte = stage + stage_bytes;                          // 128 bytes
@@ -237,8 +229,6 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(KArgs a)
     __syncthreads();
 
     const uint32_t tile_s = smem_addr(tbuf), zrow_s = smem_addr(zrow);
-    const uint32_t a_lo = lane < X ? tile_s + (uint32_t)(lane * RS) : zrow_s;
-    const uint32_t a_hi = lane + 32 < X ? tile_s + (uint32_t)((lane + 32) * RS) : zrow_s;
     const bool two_groups = X > 32;
     const long long total = a.fill_tile_start[a.n_fills];
 
@@ -257,13 +247,12 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(KArgs a)
             trace_value(a, T.tile, 11, TW);
         }
 
-        if (a.bulk_ok) {
-            if (warp == 0) {
+        if (a.use_tma) {
+            if (tid == 0) {
                 fence_proxy_async_smem();
-                if (lane == 0) mbar_arrive_expect_tx(bar, tile_load_bytes(a, T));
-                __syncwarp();
-                issue_tile_load(a, T, tbuf, bar, lane);
-                if (lane == 0) trace_stamp(a, T.tile, 1);
+                mbar_arrive_expect_tx(bar, tile_load_bytes(a));
+                issue_tile_load(a, T, tbuf, bar);
+                trace_stamp(a, T.tile, 1);
             }
             const bool ok = mbar_wait_bounded(bar, phase, kWaitLimitNs);
             phase ^= 1u;
@@ -279,8 +268,8 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(KArgs a)
 
         if (tid == 0) trace_stamp(a, T.tile, 2);
         for (int b = warp; b < NB; b += 2 * kWarps)
-            sum_block2(a, T, a_lo, a_hi, two_groups, b, b + kWarps < NB ? b + kWarps : -1, NBT, abyte, blocksum,
-                       sarr, lane);
+            sum_block2(a, T, tile_s, zrow_s, two_groups, b, b + kWarps < NB ? b + kWarps : -1, NBT, abyte,
+                       blocksum, sarr, lane);
         __syncthreads();
         if (tid == 0) trace_stamp(a, T.tile, 3);
 
@@ -308,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(KArgs a)
             asm volatile("bar.sync 1, %0;" ::"r"(kThreads) : "memory");
             if (!(a.flags & DAQ_SKIP_ISLANDS))
                 for (int bt = warp - 1; bt < NBT; bt += kWarps - 1)
-                    stage_block(a, a_lo, a_hi, two_groups, bt, W.m, W.mb, stage, lane);
+                    stage_block(a, tile_s, zrow_s, two_groups, bt, W.m, W.mb, stage, lane);
         }
         __syncthreads();
 
@@ -388,9 +377,9 @@ __device__ __forceinline__ bool pipe_wait(const KArgs &a, uint64_t *bar, uint32_
     }
 }
 
-template <int TW> static size_t pipe_smem_bytes(int X, int rs, int need_sarr)
+template <int TW> static size_t pipe_smem_bytes(int X, int slot_bytes, int rs, int need_sarr)
 {
-    size_t b = (size_t)kNIn * X * rs + rs;
+    size_t b = (size_t)kNIn * slot_bytes + rs;
     b += (size_t)kNOut * (size_t)(((TW * 2 * X + 32) + 15) & ~15);
     b += (size_t)kNMeta * ((sizeof(PipeMeta<TW>) + 15) & ~size_t(15));
     b += need_sarr ? (size_t)kNMeta * TW * 4 : 0;
@@ -401,7 +390,7 @@ template <int TW> static size_t pipe_smem_bytes(int X, int rs, int need_sarr)
 }
 
 template <int TW>
-__global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
+__global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(const __grid_constant__ KArgs a)
 {
     constexpr int NBT = TW / 8;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -412,7 +401,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
     constexpr size_t meta_bytes = (sizeof(PipeMeta<TW>) + 15) & ~size_t(15);
 
     unsigned char *in0 = smem;
-    unsigned char *zrow = in0 + (size_t)kNIn * X * RS;
+    unsigned char *zrow = in0 + (size_t)kNIn * a.slot_bytes;
     unsigned char *out0 = zrow + RS;
     unsigned char *meta0 = out0 + (size_t)kNOut * stage_bytes;
     int32_t *sarr0 = reinterpret_cast<int32_t *>(meta0 + kNMeta * meta_bytes);
@@ -495,13 +484,15 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
                 trace_value(a, T.tile, 10, sm_id());
                 trace_value(a, T.tile, 11, TW);
             }
-            unsigned char *slot = in0 + (size_t)s * X * RS;
-            if (a.bulk_ok) {
-                fence_proxy_async_smem();
-                if (lane == 0) mbar_arrive_expect_tx(bars + kBarInFull + s, tile_load_bytes(a, T));
+            unsigned char *slot = in0 + (size_t)s * a.slot_bytes;
+            if (a.use_tma) {
+                if (lane == 0) {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(bars + kBarInFull + s, tile_load_bytes(a));
+                    issue_tile_load(a, T, slot, bars + kBarInFull + s);
+                    trace_stamp(a, T.tile, 1);
+                }
                 __syncwarp();
-                issue_tile_load(a, T, slot, bars + kBarInFull + s, lane);
-                if (lane == 0) trace_stamp(a, T.tile, 1);
                 pending |= 1u << s;
                 pend_parity = (pend_parity & ~(1u << s)) | ((uint32_t)((i / kNIn) & 1) << s);
             } else {
@@ -529,12 +520,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
                 break;
             }
             if (cw == 0 && lane == 0) trace_stamp(a, T.tile, 2);
-            const uint32_t slot_s = smem_addr(in0 + (size_t)s * X * RS);
-            const uint32_t a_lo = lane < X ? slot_s + (uint32_t)(lane * RS) : zrow_s;
-            const uint32_t a_hi = lane + 32 < X ? slot_s + (uint32_t)((lane + 32) * RS) : zrow_s;
+            const uint32_t slot_s = smem_addr(in0 + (size_t)s * a.slot_bytes);
             for (int b = cw; b < NB; b += 2 * kPipeNCompute)
-                sum_block2(a, T, a_lo, a_hi, two_groups, b, b + kPipeNCompute < NB ? b + kPipeNCompute : -1, NBT,
-                           M->abyte, M->blocksum, sarr(m), lane);
+                sum_block2(a, T, slot_s, zrow_s, two_groups, b, b + kPipeNCompute < NB ? b + kPipeNCompute : -1,
+                           NBT, M->abyte, M->blocksum, sarr(m), lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(bars + kBarBits + m);
             if (cw == 0 && lane == 0) trace_stamp(a, T.tile, 3);
@@ -543,7 +532,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
             if (!skip_isl) {
                 unsigned char *stage = out0 + (size_t)o * stage_bytes;
                 for (int bt = cw; bt < NBT; bt += kPipeNCompute)
-                    stage_block(a, a_lo, a_hi, two_groups, bt, M->wm, M->wmb, stage, lane);
+                    stage_block(a, slot_s, zrow_s, two_groups, bt, M->wm, M->wmb, stage, lane);
             }
             __syncwarp();
             if (lane == 0) {
@@ -649,9 +638,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(KArgs a)
 }
 
 // ============================================================================ host side
-static size_t plain_smem_bytes(int tw, int X, int rs, int need_sarr)
+static size_t plain_smem_bytes(int tw, int X, int slot_bytes, int rs, int need_sarr)
 {
-    size_t b = (size_t)X * rs + rs;
+    size_t b = (size_t)slot_bytes + rs;
     b += (size_t)(((tw * 2 * X + 32) + 15) & ~15);
     b += 128;
     b += (size_t)(tw / 8) * 4;
@@ -661,13 +650,13 @@ static size_t plain_smem_bytes(int tw, int X, int rs, int need_sarr)
     return (b + 127) & ~size_t(127);
 }
 
-static size_t pipe_smem(int tw, int X, int rs, int need_sarr)
+static size_t pipe_smem(int tw, int X, int slot_bytes, int rs, int need_sarr)
 {
     switch (tw) {
-    case 128: return pipe_smem_bytes<128>(X, rs, need_sarr);
-    case 224: return pipe_smem_bytes<224>(X, rs, need_sarr);
-    case 448: return pipe_smem_bytes<448>(X, rs, need_sarr);
-    default: return pipe_smem_bytes<960>(X, rs, need_sarr);
+    case 128: return pipe_smem_bytes<128>(X, slot_bytes, rs, need_sarr);
+    case 224: return pipe_smem_bytes<224>(X, slot_bytes, rs, need_sarr);
+    case 448: return pipe_smem_bytes<448>(X, slot_bytes, rs, need_sarr);
+    default: return pipe_smem_bytes<960>(X, slot_bytes, rs, need_sarr);
     }
 }
 
@@ -694,21 +683,59 @@ static DeviceInfo device_info(int dev)
 constexpr int kSmemBudget = 227 * 1024;
 
 struct Plan {
-    int tw, hl, hr, ew, rs, need_sarr, pipelined;
+    int tw, hl, hr, ew, rs, boxw, nbox, box_stride, slot_bytes, need_sarr, pipelined;
     size_t smem;
     int64_t max_tiles;
 };
 
+// Extended tile = nbox TMA boxes of boxw samples: boxw <= 248 and an odd
+// multiple of 8, so a box row (2 boxw bytes) is an odd multiple of 16 bytes.
 static void plan_geometry(Plan *pl, int tw, int pre, int post, int X)
 {
     pl->tw = tw;
     pl->hl = (post + 1 + 7) & ~7;
     pl->hr = (pre + 1 + 7) & ~7;
     pl->ew = pl->hl + tw + pl->hr;
-    int rs = ((pl->ew * 2) + 15) & ~15;
-    if (((rs / 16) & 1) == 0) rs += 16;  // odd multiple of 16 bytes: conflict-free ldmatrix rows
-    pl->rs = rs;
-    pl->smem = pl->pipelined ? pipe_smem(tw, X, rs, pl->need_sarr) : plain_smem_bytes(tw, X, rs, pl->need_sarr);
+    pl->nbox = (pl->ew + 247) / 248;
+    int boxw = (((pl->ew + pl->nbox - 1) / pl->nbox) + 7) & ~7;
+    if (((boxw / 8) & 1) == 0) boxw += 8;
+    pl->boxw = boxw;
+    pl->rs = 2 * boxw;
+    pl->box_stride = (X * pl->rs + 127) & ~127;
+    pl->slot_bytes = pl->nbox * pl->box_stride;
+    pl->smem = pl->pipelined ? pipe_smem(tw, X, pl->slot_bytes, pl->rs, pl->need_sarr)
+                             : plain_smem_bytes(tw, X, pl->slot_bytes, pl->rs, pl->need_sarr);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// samples as a 2-D tensor: rows = (fill, calo, crystal), columns = samples.
+static bool encode_tensor_map(CUtensorMap *m, const int16_t *samples, int64_t rows, int64_t n_samples, int boxw,
+                              int X)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)n_samples, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)n_samples * sizeof(int16_t)};
+    cuuint32_t box[2] = {(cuuint32_t)boxw, (cuuint32_t)X};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<int16_t *>(samples), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, const daq_params *p, Plan *pl)
@@ -871,7 +898,14 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
     a.hr = pl.hr;
     a.ew = pl.ew;
     a.rs = pl.rs;
-    a.bulk_ok = (n_samples % 8 == 0) && ((reinterpret_cast<uintptr_t>(samples) & 15) == 0);
+    a.boxw = pl.boxw;
+    a.nbox = pl.nbox;
+    a.box_stride = pl.box_stride;
+    a.slot_bytes = pl.slot_bytes;
+    a.use_tma = 0;
+    if (total > 0 && n_samples % 8 == 0 && (reinterpret_cast<uintptr_t>(samples) & 15) == 0)
+        a.use_tma = encode_tensor_map(&a.tmap, samples, (int64_t)n_fills * n_calo * n_xtal, n_samples, pl.boxw,
+                                      n_xtal);
     a.need_sarr = pl.need_sarr;
     a.max_tiles = pl.max_tiles;
     a.hdr = skip_isl ? nullptr : out->hdr;

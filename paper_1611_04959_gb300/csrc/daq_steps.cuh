@@ -2,11 +2,15 @@
 // shared by the simple and the pipelined tile kernels.
 //
 // A tile is TW consecutive samples [t0, t0 + TW) of one calorimeter-fill.  Its
-// crystal rows are held in shared memory with a halo: column c of a row is
-// sample t0 - HL + c, for c in [0, EW), EW = HL + TW + HR.  Row stride RS is an
-// odd multiple of 16 bytes, so the eight rows of every ldmatrix are
-// conflict-free.
+// crystal rows are held in shared memory with a halo: extended column c is
+// sample t0 - HL + c, for c in [0, EW), EW = HL + TW + HR.  The extended tile
+// is stored as nbox boxes of [n_xtal][boxw] samples (one 2-D TMA box each, box
+// k holding columns [k boxw, (k+1) boxw)), box stride box_stride bytes.  The
+// row pitch 2 boxw is an odd multiple of 16 bytes, so the eight rows of every
+// ldmatrix are conflict-free.
 #pragma once
+
+#include <cuda.h>
 
 #include <cstdint>
 
@@ -76,6 +80,7 @@ __device__ __forceinline__ Agg shfl_down_agg(const Agg &a, int d)
 }
 
 struct KArgs {
+    CUtensorMap tmap;  // samples as a 2-D tensor [F*C*X rows][n_samples], when use_tma
     const int16_t *samples;
     int32_t n_calo, n_xtal, n_fills;
     int64_t n_samples;  // row pitch
@@ -85,8 +90,9 @@ struct KArgs {
     int32_t fill_base;
     const int32_t *fill_len;
     uint32_t flags;
-    int32_t hl, hr, ew, rs;  // halo left/right, extended width, smem row stride (bytes)
-    int32_t bulk_ok;
+    int32_t hl, hr, ew, rs;  // halo left/right, extended width, smem row pitch (bytes) = 2 boxw
+    int32_t boxw, nbox, box_stride, slot_bytes;
+    int32_t use_tma;
     int32_t need_sarr;
     int64_t max_tiles;
     // outputs
@@ -175,51 +181,22 @@ __device__ bool decode_tile(const KArgs &a, long long tile, TileInfo &T, const l
 }
 
 // --------------------------------------------------------------------------- crystal sum + threshold
-// One 8-sample block b of the extended tile (warp-wide).  Lane L of the
-// ldmatrix transposes holds crystals 8g + 2(L%4), +1 at sample L/4 of the block;
-// dp2a adds both halves, two shuffles finish the 54-crystal sum.
-__device__ __forceinline__ void sum_block(const KArgs &a, const TileInfo &T, uint32_t a_lo, uint32_t a_hi,
-                                          bool two_groups, int b, int nbt, uint8_t *abyte, int32_t *blocksum,
-                                          int32_t *sarr, int lane)
+// Shared-memory address of crystal x's 16 bytes at 8-sample block b of a tile
+// slot; crystals past n_xtal read a zero row.
+__device__ __forceinline__ uint32_t blk_addr(const KArgs &a, uint32_t slot_s, uint32_t zrow_s, int x, int b)
 {
-    const uint32_t col = 16u * (uint32_t)b;
-    uint32_t r0, r1, r2, r3, r4 = 0, r5 = 0, r6 = 0, r7 = 0;
-    ldsm_x4_trans(a_lo + col, r0, r1, r2, r3);
-    if (two_groups) ldsm_x4_trans(a_hi + col, r4, r5, r6, r7);
-    int acc = __dp2a_lo((int)r0, 0x0101, 0);
-    acc = __dp2a_lo((int)r1, 0x0101, acc);
-    acc = __dp2a_lo((int)r2, 0x0101, acc);
-    acc = __dp2a_lo((int)r3, 0x0101, acc);
-    acc = __dp2a_lo((int)r4, 0x0101, acc);
-    acc = __dp2a_lo((int)r5, 0x0101, acc);
-    acc = __dp2a_lo((int)r6, 0x0101, acc);
-    acc = __dp2a_lo((int)r7, 0x0101, acc);
-    acc += __shfl_xor_sync(kFull, acc, 1);
-    acc += __shfl_xor_sync(kFull, acc, 2);
-    const int j = lane >> 2;
-    const long long t = T.t0 - a.hl + 8 * b + j;
-    const int S = acc - T.ptot;
-    const bool cross = (t >= 0) && (t < T.len) && (S > a.threshold);
-    uint32_t v = __ballot_sync(kFull, cross) & 0x11111111u;
-    v = (v | (v >> 3)) & 0x03030303u;
-    v = (v | (v >> 6)) & 0x000f000fu;
-    v = (v | (v >> 12)) & 0xffu;
-    if (lane == 0) abyte[b] = (uint8_t)v;
-    const int bt = b - a.hl / 8;
-    if (bt >= 0 && bt < nbt) {
-        const bool in = t < T.t_end;
-        int sv = in ? S : 0;
-        sv += __shfl_xor_sync(kFull, sv, 4);
-        sv += __shfl_xor_sync(kFull, sv, 8);
-        sv += __shfl_xor_sync(kFull, sv, 16);
-        if (lane == 0) blocksum[bt] = sv;
-        if (a.need_sarr && (lane & 3) == 0 && in) sarr[8 * bt + j] = S;
-    }
+    const int c = 8 * b;
+    const int k = (c >= a.boxw) + (c >= 2 * a.boxw) + (c >= 3 * a.boxw) + (c >= 4 * a.boxw);  // nbox <= 5
+    const int col = c - k * a.boxw;
+    if (x >= a.n_xtal) return zrow_s + 2u * (uint32_t)col;
+    return slot_s + (uint32_t)(k * a.box_stride + x * a.rs + 2 * col);
 }
 
-// Two blocks at once (b1 < 0: only b0): both blocks' shared-memory loads are
-// issued before either is used.
-__device__ __forceinline__ void sum_block2(const KArgs &a, const TileInfo &T, uint32_t a_lo, uint32_t a_hi,
+// Two 8-sample blocks at once (b1 < 0: only b0), warp-wide: crystal sums,
+// threshold bits and block sums.  Lane L of the ldmatrix transposes holds
+// crystals 8g + 2(L%4), +1 at sample L/4 of a block; dp2a adds both halves and
+// two shuffles finish the crystal sum.  Both blocks' loads are issued first.
+__device__ __forceinline__ void sum_block2(const KArgs &a, const TileInfo &T, uint32_t slot_s, uint32_t zrow_s,
                                            bool two_groups, int b0, int b1, int nbt, uint8_t *abyte,
                                            int32_t *blocksum, int32_t *sarr, int lane)
 {
@@ -228,12 +205,12 @@ __device__ __forceinline__ void sum_block2(const KArgs &a, const TileInfo &T, ui
     for (int u = 0; u < 2; ++u)
 #pragma unroll
         for (int k = 0; k < 8; ++k) r[u][k] = 0u;
-    const uint32_t c0 = 16u * (uint32_t)b0, c1 = 16u * (uint32_t)(b1 >= 0 ? b1 : b0);
-    ldsm_x4_trans(a_lo + c0, r[0][0], r[0][1], r[0][2], r[0][3]);
-    if (two_groups) ldsm_x4_trans(a_hi + c0, r[0][4], r[0][5], r[0][6], r[0][7]);
+    ldsm_x4_trans(blk_addr(a, slot_s, zrow_s, lane, b0), r[0][0], r[0][1], r[0][2], r[0][3]);
+    if (two_groups) ldsm_x4_trans(blk_addr(a, slot_s, zrow_s, lane + 32, b0), r[0][4], r[0][5], r[0][6], r[0][7]);
     if (b1 >= 0) {
-        ldsm_x4_trans(a_lo + c1, r[1][0], r[1][1], r[1][2], r[1][3]);
-        if (two_groups) ldsm_x4_trans(a_hi + c1, r[1][4], r[1][5], r[1][6], r[1][7]);
+        ldsm_x4_trans(blk_addr(a, slot_s, zrow_s, lane, b1), r[1][0], r[1][1], r[1][2], r[1][3]);
+        if (two_groups)
+            ldsm_x4_trans(blk_addr(a, slot_s, zrow_s, lane + 32, b1), r[1][4], r[1][5], r[1][6], r[1][7]);
     }
     const int j = lane >> 2;
 #pragma unroll
@@ -351,7 +328,8 @@ __device__ __forceinline__ void publish(TileStatus *st, long long tile, bool inc
 __device__ __forceinline__ unsigned read_status(const TileStatus *st, long long idx, Agg &v)
 {
     unsigned long long lo, hi;
-    ld_acquire_b128(&st[idx], lo, hi);
+    // relaxed: the 16-byte word is the whole message, nothing else is read on its account
+    ld_relaxed_b128(&st[idx], lo, hi);
     const unsigned k = (unsigned)(lo & 3ull);
     if (k == 0 || k != (unsigned)(hi & 3ull)) return 0;
     v.m = (long long)(lo >> 2);
@@ -444,8 +422,8 @@ __device__ Agg look_back(const KArgs &a, long long tile, int lane, unsigned *sta
 // Block bt of the tile proper (warp-wide): every marked sample's n_xtal raw
 // values go to its row in the tile-local stage area (row = marked samples
 // before it in the tile).
-__device__ __forceinline__ void stage_block(const KArgs &a, uint32_t a_lo, uint32_t a_hi, bool two_groups, int bt,
-                                            const uint32_t *w_m, const int32_t *w_mb, unsigned char *stage,
+__device__ __forceinline__ void stage_block(const KArgs &a, uint32_t slot_s, uint32_t zrow_s, bool two_groups,
+                                            int bt, const uint32_t *w_m, const int32_t *w_mb, unsigned char *stage,
                                             int lane)
 {
     const int X = a.n_xtal;
@@ -453,10 +431,10 @@ __device__ __forceinline__ void stage_block(const KArgs &a, uint32_t a_lo, uint3
     const uint32_t mw = w_m[w];
     const uint32_t bits = (mw >> shift) & 0xffu;
     if (!bits) return;
-    const uint32_t col = 16u * (uint32_t)(bt + a.hl / 8);
+    const int b = bt + a.hl / 8;
     uint32_t r[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-    ldsm_x4_trans(a_lo + col, r[0], r[1], r[2], r[3]);
-    if (two_groups) ldsm_x4_trans(a_hi + col, r[4], r[5], r[6], r[7]);
+    ldsm_x4_trans(blk_addr(a, slot_s, zrow_s, lane, b), r[0], r[1], r[2], r[3]);
+    if (two_groups) ldsm_x4_trans(blk_addr(a, slot_s, zrow_s, lane + 32, b), r[4], r[5], r[6], r[7]);
     const int j = lane >> 2, q4 = lane & 3;
     if (!((bits >> j) & 1u)) return;
     const int rl = w_mb[w] + __popc(mw & ((1u << (shift + j)) - 1u));
