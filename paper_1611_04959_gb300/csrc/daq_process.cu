@@ -49,6 +49,17 @@ namespace daq {
 constexpr int kThreads = 256;  // prepare kernel and plain tile kernel
 constexpr int kWarps = kThreads / 32;
 
+// Staging row pitch: odd n_xtal keeps 2 n_xtal bytes; even n_xtal pads a row
+// to P words with P = 4 (mod 8), so that eight rows x four words of one
+// staging store hit 32 distinct banks.
+static int stage_row_bytes(int X)
+{
+    if (X & 1) return 2 * X;
+    int P = X / 2;
+    while ((P & 7) != 4) ++P;
+    return 4 * P;
+}
+
 // Workspace layout (byte offsets from the workspace base).
 struct WsLayout {
     size_t ticket, fts, lens, ptot, status, total;
@@ -208,8 +219,8 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(const __grid_cons
 
     unsigned char *tbuf = smem;                                    // tile slot (nbox boxes)
     unsigned char *zrow = tbuf + a.slot_bytes;                     // zero row
-    unsigned char *stage = zrow + RS;                              // TW * 2X + 32 bytes
-    const int stage_bytes = ((TW * 2 * X + 32) + 15) & ~15;
+    unsigned char *stage = zrow + RS;                              // TW rows of srow bytes + 32
+    const int stage_bytes = ((TW * a.srow + 32) + 15) & ~15;
     uint8_t *abyte = stage + stage_bytes;                          // 128 bytes
     int32_t *blocksum = reinterpret_cast<int32_t *>(abyte + 128);  // NBT
     int32_t *sarr = blocksum + NBT;                                // TW when needed
@@ -380,7 +391,7 @@ __device__ __forceinline__ bool pipe_wait(const KArgs &a, uint64_t *bar, uint32_
 template <int TW> static size_t pipe_smem_bytes(int X, int slot_bytes, int rs, int need_sarr)
 {
     size_t b = (size_t)kNIn * slot_bytes + rs;
-    b += (size_t)kNOut * (size_t)(((TW * 2 * X + 32) + 15) & ~15);
+    b += (size_t)kNOut * (size_t)(((TW * stage_row_bytes(X) + 32) + 15) & ~15);
     b += (size_t)kNMeta * ((sizeof(PipeMeta<TW>) + 15) & ~size_t(15));
     b += need_sarr ? (size_t)kNMeta * TW * 4 : 0;
     b += (size_t)kNBars * 8 + 16;
@@ -397,7 +408,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(const __grid_
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int X = a.n_xtal, RS = a.rs;
     const int NB = a.ew / 8;
-    const int stage_bytes = ((TW * 2 * X + 32) + 15) & ~15;
+    const int stage_bytes = ((TW * a.srow + 32) + 15) & ~15;
     constexpr size_t meta_bytes = (sizeof(PipeMeta<TW>) + 15) & ~size_t(15);
 
     unsigned char *in0 = smem;
@@ -641,7 +652,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(const __grid_
 static size_t plain_smem_bytes(int tw, int X, int slot_bytes, int rs, int need_sarr)
 {
     size_t b = (size_t)slot_bytes + rs;
-    b += (size_t)(((tw * 2 * X + 32) + 15) & ~15);
+    b += (size_t)(((tw * stage_row_bytes(X) + 32) + 15) & ~15);
     b += 128;
     b += (size_t)(tw / 8) * 4;
     b += need_sarr ? (size_t)tw * 4 : 0;
@@ -902,6 +913,9 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
     a.nbox = pl.nbox;
     a.box_stride = pl.box_stride;
     a.slot_bytes = pl.slot_bytes;
+    a.srow = stage_row_bytes(n_xtal);
+    a.wpr = n_xtal / 2;
+    a.wpr_mul = a.wpr > 0 ? (uint32_t)((1ull << 32) / (uint64_t)a.wpr + 1) : 0u;
     a.use_tma = 0;
     if (total > 0 && n_samples % 8 == 0 && (reinterpret_cast<uintptr_t>(samples) & 15) == 0)
         a.use_tma = encode_tensor_map(&a.tmap, samples, (int64_t)n_fills * n_calo * n_xtal, n_samples, pl.boxw,

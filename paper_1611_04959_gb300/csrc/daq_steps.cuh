@@ -93,6 +93,10 @@ struct KArgs {
     int32_t hl, hr, ew, rs;  // halo left/right, extended width, smem row pitch (bytes) = 2 boxw
     int32_t boxw, nbox, box_stride, slot_bytes;
     int32_t use_tma;
+    // stage rows: pitch srow bytes; for even n_xtal, wpr words of data per row
+    // and a pitch of srow/4 words = 4 (mod 8), so staging stores are conflict-free
+    int32_t srow, wpr;
+    uint32_t wpr_mul;  // floor(2^32 / wpr) + 1, for w / wpr
     int32_t need_sarr;
     int64_t max_tiles;
     // outputs
@@ -243,6 +247,82 @@ __device__ __forceinline__ void sum_block2(const KArgs &a, const TileInfo &T, ui
     }
 }
 
+// Marks of the 32 extended-tile bits held by this lane: M[i] = OR of A over
+// [i - post, i + pre].  Fast form (post + pre <= 96): the lane gathers the seven
+// threshold words around its own once and widens them in registers.
+__device__ __forceinline__ uint32_t marks_word(const KArgs &a, uint32_t A, int lane)
+{
+    const int L = a.pre + a.post + 1;
+    if (a.pre + a.post <= 96) {
+        uint32_t win[8];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+            const int src = lane + i - 3;
+            const uint32_t v = __shfl_sync(kFull, A, src & 31);
+            win[i] = (src >= 0 && src < 32) ? v : 0u;
+        }
+        win[7] = 0u;
+        // V = bits [32 lane - post, 32 lane - post + 128) of the threshold array
+        const int o = 96 - a.post, qw = o >> 5, sw = o & 31;
+        // drop the qw lowest words (uniform qw in 0..3) with constant-index moves
+        if (qw & 2) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) win[k] = win[k + 2];
+            win[6] = win[7] = 0u;
+        }
+        if (qw & 1) {
+#pragma unroll
+            for (int k = 0; k < 7; ++k) win[k] = win[k + 1];
+            win[7] = 0u;
+        }
+        uint32_t v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = sw ? __funnelshift_r(win[i], win[i + 1], sw) : win[i];
+        unsigned long long rlo = ((unsigned long long)v[1] << 32) | v[0];
+        unsigned long long rhi = ((unsigned long long)v[3] << 32) | v[2];
+        auto shr128 = [](unsigned long long &lo, unsigned long long &hi, int sft) {
+            if (sft >= 64) {
+                lo = hi >> (sft - 64);
+                hi = 0ull;
+            } else if (sft > 0) {
+                lo = (lo >> sft) | (hi << (64 - sft));
+                hi >>= sft;
+            }
+        };
+        // OR of L consecutive bits by doubling
+        int cov = 1;
+        while (2 * cov <= L) {
+            unsigned long long tlo = rlo, thi = rhi;
+            shr128(tlo, thi, cov);
+            rlo |= tlo;
+            rhi |= thi;
+            cov *= 2;
+        }
+        if (cov < L) {
+            unsigned long long tlo = rlo, thi = rhi;
+            shr128(tlo, thi, L - cov);
+            rlo |= tlo;
+        }
+        return (uint32_t)rlo;
+    }
+    // general form: forward spread by post, backward spread by pre, across the warp
+    uint32_t Fv = A;
+    int cov = 1;
+    while (2 * cov <= a.post + 1) {
+        Fv |= shl_bits(Fv, cov, lane);
+        cov *= 2;
+    }
+    if (cov < a.post + 1) Fv |= shl_bits(Fv, a.post + 1 - cov, lane);
+    uint32_t Mv = Fv;
+    cov = 1;
+    while (2 * cov <= a.pre + 1) {
+        Mv |= shr_bits(Mv, cov, lane);
+        cov *= 2;
+    }
+    if (cov < a.pre + 1) Mv |= shr_bits(Mv, a.pre + 1 - cov, lane);
+    return Mv;
+}
+
 // --------------------------------------------------------------------------- windows + merge (one warp)
 // From the threshold bits of the extended tile: marks M (crossings widened by
 // pre/post samples), island starts and ends inside the tile, prefix counts per
@@ -256,58 +336,57 @@ __device__ __forceinline__ Agg tile_bits(const KArgs &a, const TileInfo &T, cons
     const int NWE = (a.ew + 31) / 32;
     const long long e0 = T.t0 - HL;
     const uint32_t A = lane < NWE ? reinterpret_cast<const uint32_t *>(abyte)[lane] : 0u;
-    // forward spread: F[i] = OR_{k=0..post} A[i-k]
-    uint32_t Fv = A;
-    int cov = 1;
-    while (2 * cov <= a.post + 1) {
-        Fv |= shl_bits(Fv, cov, lane);
-        cov *= 2;
-    }
-    if (cov < a.post + 1) Fv |= shl_bits(Fv, a.post + 1 - cov, lane);
-    // backward spread: M[i] = OR_{k=0..pre} F[i+k]
-    uint32_t Mv = Fv;
-    cov = 1;
-    while (2 * cov <= a.pre + 1) {
-        Mv |= shr_bits(Mv, cov, lane);
-        cov *= 2;
-    }
-    if (cov < a.pre + 1) Mv |= shr_bits(Mv, a.pre + 1 - cov, lane);
+    uint32_t Mv = marks_word(a, A, lane);
     Mv &= range_mask(32ll * lane, -e0, T.len - e0);  // only samples of [0, len) are marked
-    const uint32_t m_prev = (__shfl_sync(kFull, Mv, (HL - 1) >> 5) >> ((HL - 1) & 31)) & 1u;
-    const uint32_t m_next = (__shfl_sync(kFull, Mv, (HL + TW) >> 5) >> ((HL + TW) & 31)) & 1u;
+    const uint32_t prev_w = __shfl_sync(kFull, Mv, (HL - 1) >> 5);
+    const uint32_t next_w = __shfl_sync(kFull, Mv, (HL + TW) >> 5);
     const int qo = HL >> 5, sh = HL & 31;
     uint32_t lo_w = __shfl_down_sync(kFull, Mv, qo);
     uint32_t hi_w = __shfl_down_sync(kFull, Mv, qo + 1 < 32 ? qo + 1 : 31);
+    const uint32_t m_prev = (prev_w >> ((HL - 1) & 31)) & 1u;
+    const uint32_t m_next = (next_w >> ((HL + TW) & 31)) & 1u;
     if (lane + qo > 31) lo_w = 0u;
     if (lane + qo + 1 > 31) hi_w = 0u;
     uint32_t Mt = sh ? ((lo_w >> sh) | (hi_w << (32 - sh))) : lo_w;
     if (lane >= NWT) Mt = 0u;
     uint32_t below = __shfl_up_sync(kFull, Mt, 1);
-    if (lane == 0) below = m_prev << 31;
     uint32_t above = __shfl_down_sync(kFull, Mt, 1);
+    if (lane == 0) below = m_prev << 31;
     if (lane == NWT - 1) above = m_next;
     if (lane >= NWT) above = 0u;
     const uint32_t St = Mt & ~((Mt << 1) | (below >> 31));
     const uint32_t Et = Mt & ~((Mt >> 1) | (above << 31));
-    int m_tot, s_tot;
-    const int mb = warp_excl_scan_add<int>(__popc(Mt), lane, m_tot);
-    const int sb = warp_excl_scan_add<int>(__popc(St), lane, s_tot);
-    const int last_start = St ? 32 * lane + 31 - __clz(St) : -1;
-    const int ls = warp_excl_scan_max(last_start, lane, -1);
+    // one scan for both counts (each <= 1024): marked in the low half, starts in the high half
+    const uint32_t packed = (uint32_t)__popc(Mt) | ((uint32_t)__popc(St) << 16);
+    uint32_t x = packed;
+    int mx = St ? 32 * lane + 31 - __clz(St) : -1;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, d);
+        const int ym = __shfl_up_sync(kFull, mx, d);
+        if (lane >= d) {
+            x += y;
+            mx = max(mx, ym);
+        }
+    }
+    const uint32_t tot = __shfl_sync(kFull, x, 31);
+    const int ls_incl_prev = __shfl_up_sync(kFull, mx, 1);
+    const uint32_t excl = x - packed;
+    const int ls = lane == 0 ? -1 : ls_incl_prev;
     const int nt = (int)(T.t_end - T.t0);
     const uint32_t zeros = ~Mt & range_mask(32ll * lane, 0, nt);
-    const int lz = warp_max(zeros ? 32 * lane + 31 - __clz(zeros) : -1);
+    const int lz = (int)__reduce_max_sync(kFull, zeros ? (unsigned)(32 * lane + 32 - __clz(zeros)) : 0u) - 1;
     if (lane < NWT) {
         w.m[lane] = Mt;
         w.s[lane] = St;
         w.e[lane] = Et;
-        w.mb[lane] = mb;
-        w.sb[lane] = sb;
+        w.mb[lane] = (int)(excl & 0xffffu);
+        w.sb[lane] = (int)(excl >> 16);
         w.ls[lane] = ls;
     }
     Agg agg;
-    agg.m = m_tot;
-    agg.s = s_tot;
+    agg.m = tot & 0xffffu;
+    agg.s = tot >> 16;
     agg.tr = nt - 1 - lz;
     agg.full = (lz < 0) && m_prev;
     agg.poison = 0;
@@ -342,18 +421,21 @@ __device__ __forceinline__ unsigned read_status(const TileStatus *st, long long 
 
 // Decoupled look-back (one warp): exclusive prefix of `tile` over all earlier
 // tiles.  Each round reads 128 predecessors (4 per lane, one 16-byte load
-// each), stops at the nearest inclusive prefix, and combines the aggregates in
-// between in order.  Bounded: gives up after kWaitLimitNs or once another CTA
-// has flagged a timeout, returning a poisoned prefix.
+// each).  It stops at the nearest inclusive prefix (g = stop, counting back
+// from the latest); the window's combination is formed with warp reductions:
+// marked and start counts add up, and the trailing run adds the runs of the
+// latest entries up to and including the first one that is not fully marked.
+// Bounded: gives up after kWaitLimitNs or once another CTA has flagged a
+// timeout, returning a poisoned prefix.
 __device__ Agg look_back(const KArgs &a, long long tile, int lane, unsigned *stats = nullptr)
 {
-    constexpr int PER = 4;
-    unsigned rounds = 0, waits = 0;
+    constexpr int PER = 4, BIG = 1 << 20;
     const TileStatus *st = a.status;
     long long pos = tile - 1;
     Agg acc = agg_identity();
     uint64_t t_start = 0;
     bool waiting = false;
+    unsigned rounds = 0, waits = 0;
     for (uint32_t iter = 0;; ++iter) {
         unsigned kind[PER];
         Agg v[PER];
@@ -361,24 +443,20 @@ __device__ Agg look_back(const KArgs &a, long long tile, int lane, unsigned *sta
         for (int j = 0; j < PER; ++j) {
             const long long idx = pos - (PER * lane + j);
             v[j] = agg_identity();
-            kind[j] = kKindInc;
+            v[j].full = 0;
+            kind[j] = kKindInc;  // before tile 0: an empty inclusive prefix
             if (idx >= 0) kind[j] = read_status(st, idx, v[j]);
         }
-        // nearest inclusive prefix g = PER * lane + j
-        int first_inc = 1 << 30, first_missing = 1 << 30;
+        int my_stop = BIG, my_miss = BIG;
 #pragma unroll
         for (int j = PER - 1; j >= 0; --j) {
-            if (kind[j] >= kKindInc) first_inc = PER * lane + j;
-            if (kind[j] == 0) first_missing = PER * lane + j;
+            if (kind[j] >= kKindInc) my_stop = PER * lane + j;
+            if (kind[j] == 0) my_miss = PER * lane + j;
         }
-        int stop = first_inc, missing = first_missing;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            stop = min(stop, __shfl_xor_sync(kFull, stop, d));
-            missing = min(missing, __shfl_xor_sync(kFull, missing, d));
-        }
-        const int last_needed = stop < (1 << 30) ? stop : 32 * PER - 1;
-        if (missing <= last_needed) {
+        const int stop = (int)__reduce_min_sync(kFull, (unsigned)my_stop);
+        const int missing = (int)__reduce_min_sync(kFull, (unsigned)my_miss);
+        const int last = stop < BIG ? stop : 32 * PER - 1;
+        if (missing <= last) {
             // a needed predecessor has published nothing yet: wait (bounded)
             ++waits;
             if (!waiting) {
@@ -395,21 +473,44 @@ __device__ Agg look_back(const KArgs &a, long long tile, int lane, unsigned *sta
             }
             continue;
         }
-        // this lane's entries up to last_needed, in order (latest last)
-        Agg lane_acc = agg_identity();
+        // first entry (from the latest) that is not fully marked, within [0, last]
+        int my_nf = BIG;
 #pragma unroll
         for (int j = PER - 1; j >= 0; --j)
-            if (PER * lane + j <= last_needed) lane_acc = combine(lane_acc, v[j]);
-        // ordered reduction over lanes: higher lanes hold earlier tiles
+            if (PER * lane + j <= last && !v[j].full) my_nf = PER * lane + j;
+        const int nf = (int)__reduce_min_sync(kFull, (unsigned)my_nf);
+        const int gstar = nf < last ? nf : last;
+        unsigned m_agg = 0, s_agg = 0, tr_sum = 0;
+        long long m_inc = 0, s_inc = 0;
+        int poison = 0;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const Agg other = shfl_down_agg(lane_acc, d);
-            if ((lane & (2 * d - 1)) == 0 && lane + d < 32) lane_acc = combine(other, lane_acc);
+        for (int j = 0; j < PER; ++j) {
+            const int g = PER * lane + j;
+            if (g > last) continue;
+            if (g == stop) {
+                m_inc = v[j].m;
+                s_inc = v[j].s;
+            } else {
+                m_agg += (unsigned)v[j].m;  // aggregates: at most 127 tiles of <= 960 samples
+                s_agg += (unsigned)v[j].s;
+            }
+            if (g <= gstar) tr_sum += (unsigned)v[j].tr;
+            poison |= v[j].poison;
         }
-        const Agg window = shfl_agg(lane_acc, 0);
+        Agg window;
+        window.m = (long long)__reduce_add_sync(kFull, m_agg);
+        window.s = (long long)__reduce_add_sync(kFull, s_agg);
+        window.tr = (long long)__reduce_add_sync(kFull, tr_sum);
+        window.full = nf > last;
+        window.poison = __any_sync(kFull, poison);
+        if (stop < BIG) {
+            const int src = stop / PER;
+            window.m += __shfl_sync(kFull, m_inc, src);
+            window.s += __shfl_sync(kFull, s_inc, src);
+        }
         acc = combine(window, acc);
         ++rounds;
-        if (stop < (1 << 30)) {
+        if (stop < BIG) {
             if (stats) *stats = rounds * 100000u + waits;
             return acc;
         }
@@ -438,12 +539,11 @@ __device__ __forceinline__ void stage_block(const KArgs &a, uint32_t slot_s, uin
     const int j = lane >> 2, q4 = lane & 3;
     if (!((bits >> j) & 1u)) return;
     const int rl = w_mb[w] + __popc(mw & ((1u << (shift + j)) - 1u));
-    unsigned char *dst = stage + (size_t)rl * (2 * X);
+    unsigned char *dst = stage + (size_t)rl * a.srow;
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
-        if (g >= 4 && !two_groups) break;
         const int x = 8 * g + 2 * q4;
-        if (x >= X) continue;
+        if ((g >= 4 && !two_groups) || x >= X) continue;
         if (x + 1 < X && !(X & 1)) {
             *reinterpret_cast<uint32_t *>(dst + 2 * x) = r[g];
         } else {
@@ -476,9 +576,72 @@ __device__ __forceinline__ uint4 shifted_chunk(const unsigned char *p, int e)
 // Rows [excl.m, excl.m + agg.m) from the stage area (a group of nthr threads,
 // id gt).  The body goes out in aligned 16-byte stores; the head and tail
 // (< 16 bytes each, shared with neighbouring tiles' rows) in 2-byte stores.
+// Even n_xtal: rows are wpr words; stage row r holds them at word r * P (P =
+// srow / 4), so output word w comes from stage word (w / wpr) * P + w % wpr.
+__device__ __forceinline__ void copy_out_words(const KArgs &a, const unsigned char *stage, const Agg &excl,
+                                               const Agg &agg, int gt, int nthr)
+{
+    const uint32_t *sw = reinterpret_cast<const uint32_t *>(stage);
+    const int P = a.srow >> 2, wpr = a.wpr;
+    const long long G0 = excl.m * wpr;  // global word of the tile's first output word
+    long long n_words = agg.m * wpr;
+    const long long cap_w = a.pool_cap * wpr;
+    if (G0 + n_words > cap_w) {
+        n_words = cap_w - G0;
+        if (gt == 0) set_status_bit(a, DAQ_DEV_POOL_OVERFLOW);
+    }
+    if (n_words <= 0) return;
+    uint32_t *g32 = reinterpret_cast<uint32_t *>(a.pool) + G0;
+    auto src = [&](uint32_t w) {
+        uint32_t r = __umulhi(w, a.wpr_mul);
+        if (r * (uint32_t)wpr > w) --r;
+        return r * (uint32_t)P + (w - r * (uint32_t)wpr);
+    };
+    const int head = (int)min((long long)((4 - (G0 & 3)) & 3), n_words);
+    const long long n_chunks = (n_words - head) >> 2;
+    const long long tail0 = head + 4 * n_chunks;
+    const int n_tail = (int)(n_words - tail0);
+    if (gt < head) g32[gt] = sw[src((uint32_t)gt)];
+    else if (gt >= 4 && gt < 4 + n_tail) g32[tail0 + gt - 4] = sw[src((uint32_t)(tail0 + gt - 4))];
+    constexpr int U = 4;
+    for (long long c0 = gt; c0 < n_chunks; c0 += (long long)U * nthr) {
+        uint4 out[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long c = c0 + (long long)u * nthr;
+            out[u] = make_uint4(0u, 0u, 0u, 0u);
+            if (c < n_chunks) {
+                const uint32_t w = (uint32_t)(head + 4 * c);
+                uint32_t r = __umulhi(w, a.wpr_mul);
+                if (r * (uint32_t)wpr > w) --r;
+                uint32_t k = w - r * (uint32_t)wpr, base = r * (uint32_t)P;
+                uint32_t vals[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    vals[e] = sw[base + k];
+                    if (++k == (uint32_t)wpr) {
+                        k = 0;
+                        base += P;
+                    }
+                }
+                out[u] = make_uint4(vals[0], vals[1], vals[2], vals[3]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long c = c0 + (long long)u * nthr;
+            if (c < n_chunks) st_global_cs_v4(g32 + head + 4 * c, out[u].x, out[u].y, out[u].z, out[u].w);
+        }
+    }
+}
+
 __device__ __forceinline__ void copy_out(const KArgs &a, const unsigned char *stage, const Agg &excl,
                                          const Agg &agg, int gt, int nthr)
 {
+    if (!(a.n_xtal & 1)) {
+        copy_out_words(a, stage, excl, agg, gt, nthr);
+        return;
+    }
     const long long rb = 2ll * a.n_xtal;
     const long long cap_b = a.pool_cap * rb;
     const long long gs = excl.m * rb;
