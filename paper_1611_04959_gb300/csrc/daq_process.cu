@@ -915,7 +915,7 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
     a.slot_bytes = pl.slot_bytes;
     a.srow = stage_row_bytes(n_xtal);
     a.wpr = n_xtal / 2;
-    a.wpr_mul = a.wpr > 0 ? (uint32_t)((1ull << 32) / (uint64_t)a.wpr + 1) : 0u;
+    a.wpr_mul = a.wpr > 0 ? (1ull << 32) / (unsigned long long)a.wpr + 1 : 0ull;
     a.use_tma = 0;
     if (total > 0 && n_samples % 8 == 0 && (reinterpret_cast<uintptr_t>(samples) & 15) == 0)
         a.use_tma = encode_tensor_map(&a.tmap, samples, (int64_t)n_fills * n_calo * n_xtal, n_samples, pl.boxw,

@@ -96,7 +96,7 @@ struct KArgs {
     // stage rows: pitch srow bytes; for even n_xtal, wpr words of data per row
     // and a pitch of srow/4 words = 4 (mod 8), so staging stores are conflict-free
     int32_t srow, wpr;
-    uint32_t wpr_mul;  // floor(2^32 / wpr) + 1, for w / wpr
+    unsigned long long wpr_mul;  // floor(2^32 / wpr) + 1, for w / wpr (w < 2^16)
     int32_t need_sarr;
     int64_t max_tiles;
     // outputs
@@ -592,9 +592,13 @@ __device__ __forceinline__ void copy_out_words(const KArgs &a, const unsigned ch
     }
     if (n_words <= 0) return;
     uint32_t *g32 = reinterpret_cast<uint32_t *>(a.pool) + G0;
-    auto src = [&](uint32_t w) {
-        uint32_t r = __umulhi(w, a.wpr_mul);
+    auto row_of = [&](uint32_t w) {
+        uint32_t r = (uint32_t)(((unsigned long long)w * a.wpr_mul) >> 32);
         if (r * (uint32_t)wpr > w) --r;
+        return r;
+    };
+    auto src = [&](uint32_t w) {
+        const uint32_t r = row_of(w);
         return r * (uint32_t)P + (w - r * (uint32_t)wpr);
     };
     const int head = (int)min((long long)((4 - (G0 & 3)) & 3), n_words);
@@ -612,8 +616,7 @@ __device__ __forceinline__ void copy_out_words(const KArgs &a, const unsigned ch
             out[u] = make_uint4(0u, 0u, 0u, 0u);
             if (c < n_chunks) {
                 const uint32_t w = (uint32_t)(head + 4 * c);
-                uint32_t r = __umulhi(w, a.wpr_mul);
-                if (r * (uint32_t)wpr > w) --r;
+                const uint32_t r = row_of(w);
                 uint32_t k = w - r * (uint32_t)wpr, base = r * (uint32_t)P;
                 uint32_t vals[4];
 #pragma unroll
