@@ -377,8 +377,8 @@ __device__ __forceinline__ bool pipe_wait(const KArgs &a, uint64_t *bar, uint32_
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t i = 0;; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 15u) == 15u) {
+        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+        if ((i & 3u) == 3u) {
             if (global_ns() - t0 > kWaitLimitNs) {
                 set_status_bit(a, DAQ_DEV_TIMEOUT);
                 return false;
@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(const __grid_
             bool ready = false, done = false;
             const uint64_t t0 = global_ns();
             for (uint32_t k = 0; !ready && !done; ++k) {
-                ready = mbar_try_wait(bars + kBarAgg + m, (uint32_t)((i / kNMeta) & 1));
+                ready = mbar_try_wait_sleep(bars + kBarAgg + m, (uint32_t)((i / kNMeta) & 1), 2000u);
                 if (!ready && *s_end < i) done = true;
                 if (!ready && (k & 15u) == 15u) {
                     if (global_ns() - t0 > kWaitLimitNs) {

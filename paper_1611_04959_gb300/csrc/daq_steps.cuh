@@ -471,6 +471,7 @@ __device__ Agg look_back(const KArgs &a, long long tile, int lane, unsigned *sta
                     return acc;
                 }
             }
+            __nanosleep(100);
             continue;
         }
         // first entry (from the latest) that is not fully marked, within [0, last]
