@@ -49,14 +49,13 @@ namespace daq {
 constexpr int kThreads = 256;  // prepare kernel and plain tile kernel
 constexpr int kWarps = kThreads / 32;
 
-// Staging row pitch: odd n_xtal keeps 2 n_xtal bytes; even n_xtal pads a row
-// to P words with P = 4 (mod 8), so that eight rows x four words of one
-// staging store hit 32 distinct banks.
+// Stage row pitch: P words, P the first odd number >= ceil(n_xtal / 2).  A warp's
+// staging store writes one word into each of 32 rows 2 apart, which an odd P
+// spreads over 16 banks (2-way conflicts at worst).
 static int stage_row_bytes(int X)
 {
-    if (X & 1) return 2 * X;
-    int P = X / 2;
-    while ((P & 7) != 4) ++P;
+    int P = (X + 1) / 2;
+    if (!(P & 1)) ++P;
     return 4 * P;
 }
 
@@ -214,12 +213,9 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(const __grid_cons
     constexpr int NBT = TW / 8;
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int X = a.n_xtal, RS = a.rs;
-    const int NB = a.ew / 8;
 
     unsigned char *tbuf = smem;                                    // tile slot (nbox boxes)
-    unsigned char *zrow = tbuf + a.slot_bytes;                     // zero row
-    unsigned char *stage = zrow + RS;                              // TW rows of srow bytes + 32
+    unsigned char *stage = tbuf + a.slot_bytes;                    // TW rows of srow bytes + 32
     const int stage_bytes = ((TW * a.srow + 32) + 15) & ~15;
     uint8_t *abyte = stage + stage_bytes;                          // 128 bytes
     int32_t *blocksum = reinterpret_cast<int32_t *>(abyte + 128);  // NBT
@@ -227,11 +223,11 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(const __grid_cons
     uint32_t *wm = reinterpret_cast<uint32_t *>(sarr + (a.need_sarr ? TW : 0));
     TileWords W{wm, wm + NWT, wm + 2 * NWT, reinterpret_cast<int32_t *>(wm + 3 * NWT),
                 reinterpret_cast<int32_t *>(wm + 4 * NWT), reinterpret_cast<int32_t *>(wm + 5 * NWT)};
-    TileInfo *tinfo = reinterpret_cast<TileInfo *>((reinterpret_cast<uintptr_t>(wm + 6 * NWT) + 15) & ~uintptr_t(15));
+    int16_t *rowtab = reinterpret_cast<int16_t *>(wm + 6 * NWT);  // TW
+    TileInfo *tinfo = reinterpret_cast<TileInfo *>((reinterpret_cast<uintptr_t>(rowtab + TW) + 15) & ~uintptr_t(15));
     Agg *s_agg = reinterpret_cast<Agg *>(tinfo + 1);  // [0] aggregate, [1] exclusive prefix
     uint64_t *bar = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(s_agg + 2) + 15) & ~uintptr_t(15));
 
-    for (int i = tid; i < RS / 4; i += kThreads) reinterpret_cast<uint32_t *>(zrow)[i] = 0u;
     for (int i = tid; i < 32; i += kThreads) reinterpret_cast<uint32_t *>(abyte)[i] = 0u;
     if (tid == 0) {
         mbar_init(bar, 1);
@@ -239,8 +235,9 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(const __grid_cons
     }
     __syncthreads();
 
-    const uint32_t tile_s = smem_addr(tbuf), zrow_s = smem_addr(zrow);
-    const bool two_groups = X > 32;
+    const uint32_t tile_s = smem_addr(tbuf);
+    const int n_steps = (a.ew + 63) / 64;
+    const bool skip_isl = (a.flags & DAQ_SKIP_ISLANDS) != 0;
     const long long total = a.fill_tile_start[a.n_fills];
 
     uint32_t phase = 0;
@@ -278,20 +275,17 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(const __grid_cons
         }
 
         if (tid == 0) trace_stamp(a, T.tile, 2);
-        for (int b = warp; b < NB; b += 2 * kWarps)
-            sum_block2(a, T, tile_s, zrow_s, two_groups, b, b + kWarps < NB ? b + kWarps : -1, NBT, abyte,
-                       blocksum, sarr, lane);
+        for (int it = warp; it < n_steps; it += kWarps)
+            sum_pass_step(a, T, tile_s, it, NBT, abyte, blocksum, sarr, skip_isl ? nullptr : stage, lane);
         __syncthreads();
         if (tid == 0) trace_stamp(a, T.tile, 3);
 
         if (warp == 0) {
-            const Agg agg = tile_bits<TW>(a, T, abyte, W, lane);
+            const Agg agg = tile_bits<TW>(a, T, abyte, W, rowtab, lane);
             if (lane == 0) {
                 trace_stamp(a, T.tile, 4);
                 trace_stamp(a, T.tile, 5);
             }
-            __syncwarp();
-            asm volatile("bar.arrive 1, %0;" ::"r"(kThreads) : "memory");
             Agg excl = agg_identity();
             if (T.tile > 0) {
                 if (lane == 0) publish(a.status, T.tile, false, agg);
@@ -305,10 +299,6 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(const __grid_cons
             }
         } else {
             if (!(a.flags & DAQ_SKIP_Q)) q_partial(a, T, blocksum, sarr, tid - 32, kThreads - 32);
-            asm volatile("bar.sync 1, %0;" ::"r"(kThreads) : "memory");
-            if (!(a.flags & DAQ_SKIP_ISLANDS))
-                for (int bt = warp - 1; bt < NBT; bt += kWarps - 1)
-                    stage_block(a, tile_s, zrow_s, two_groups, bt, W.m, W.mb, stage, lane);
         }
         __syncthreads();
 
@@ -317,8 +307,8 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(const __grid_cons
             trace_stamp(a, T.tile, 7);
             trace_stamp(a, T.tile, 8);
         }
-        if (!excl.poison && !(a.flags & DAQ_SKIP_ISLANDS)) {
-            copy_out(a, stage, excl, agg, tid, kThreads);
+        if (!excl.poison && !skip_isl) {
+            copy_out(a, stage, rowtab, excl, agg, tid, kThreads);
             if (warp == 0) write_headers<TW>(a, T, W, excl, lane);
         }
         if (tid == 0) trace_stamp(a, T.tile, 9);
@@ -350,6 +340,7 @@ template <int TW> struct PipeMeta {
     int32_t blocksum[TW / 8];
     uint32_t wm[TW / 32], ws[TW / 32], we[TW / 32];
     int32_t wmb[TW / 32], wsb[TW / 32], wls[TW / 32];
+    int16_t rowtab[TW];
 };
 
 // mbarrier indices
@@ -390,7 +381,7 @@ __device__ __forceinline__ bool pipe_wait(const KArgs &a, uint64_t *bar, uint32_
 
 template <int TW> static size_t pipe_smem_bytes(int X, int slot_bytes, int rs, int need_sarr)
 {
-    size_t b = (size_t)kNIn * slot_bytes + rs;
+    size_t b = (size_t)kNIn * slot_bytes;
     b += (size_t)kNOut * (size_t)(((TW * stage_row_bytes(X) + 32) + 15) & ~15);
     b += (size_t)kNMeta * ((sizeof(PipeMeta<TW>) + 15) & ~size_t(15));
     b += need_sarr ? (size_t)kNMeta * TW * 4 : 0;
@@ -406,14 +397,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(const __grid_
     constexpr int NBT = TW / 8;
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int X = a.n_xtal, RS = a.rs;
-    const int NB = a.ew / 8;
     const int stage_bytes = ((TW * a.srow + 32) + 15) & ~15;
     constexpr size_t meta_bytes = (sizeof(PipeMeta<TW>) + 15) & ~size_t(15);
 
     unsigned char *in0 = smem;
-    unsigned char *zrow = in0 + (size_t)kNIn * a.slot_bytes;
-    unsigned char *out0 = zrow + RS;
+    unsigned char *out0 = in0 + (size_t)kNIn * a.slot_bytes;
     unsigned char *meta0 = out0 + (size_t)kNOut * stage_bytes;
     int32_t *sarr0 = reinterpret_cast<int32_t *>(meta0 + kNMeta * meta_bytes);
     uint64_t *bars = reinterpret_cast<uint64_t *>(
@@ -438,7 +426,6 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(const __grid_
         return TileWords{M->wm, M->ws, M->we, M->wmb, M->wsb, M->wls};
     };
 
-    for (int i = tid; i < RS / 4; i += kPipeThreads) reinterpret_cast<uint32_t *>(zrow)[i] = 0u;
     for (int m = 0; m < kNMeta; ++m)
         for (int i = tid; i < 32; i += kPipeThreads) reinterpret_cast<uint32_t *>(meta(m)->abyte)[i] = 0u;
     if (tid == 0) {
@@ -518,10 +505,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(const __grid_
     } else if (warp >= kPipeCompute0 && warp < kPipeCompute0 + kPipeNCompute) {
         // ------------------------------------------------------------ crystal sums + staging
         const int cw = warp - kPipeCompute0;
-        const bool two_groups = X > 32;
-        const uint32_t zrow_s = smem_addr(zrow);
+        const int n_steps = (a.ew + 63) / 64;
         for (long long i = 0;; ++i) {
             const int s = (int)(i % kNIn), m = (int)(i % kNMeta), o = (int)(i % kNOut);
+            if (i >= kNOut && !pipe_wait(a, bars + kBarOutEmpty + o, (uint32_t)((i / kNOut - 1) & 1))) break;
             if (!pipe_wait(a, bars + kBarInFull + s, (uint32_t)((i / kNIn) & 1))) break;
             PipeMeta<TW> *M = meta(m);
             const TileInfo T = M->T;
@@ -532,24 +519,18 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(const __grid_
             }
             if (cw == 0 && lane == 0) trace_stamp(a, T.tile, 2);
             const uint32_t slot_s = smem_addr(in0 + (size_t)s * a.slot_bytes);
-            for (int b = cw; b < NB; b += 2 * kPipeNCompute)
-                sum_block2(a, T, slot_s, zrow_s, two_groups, b, b + kPipeNCompute < NB ? b + kPipeNCompute : -1,
-                           NBT, M->abyte, M->blocksum, sarr(m), lane);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bars + kBarBits + m);
-            if (cw == 0 && lane == 0) trace_stamp(a, T.tile, 3);
-            if (!pipe_wait(a, bars + kBarWords + m, (uint32_t)((i / kNMeta) & 1))) break;
-            if (i >= kNOut && !pipe_wait(a, bars + kBarOutEmpty + o, (uint32_t)((i / kNOut - 1) & 1))) break;
-            if (!skip_isl) {
-                unsigned char *stage = out0 + (size_t)o * stage_bytes;
-                for (int bt = cw; bt < NBT; bt += kPipeNCompute)
-                    stage_block(a, slot_s, zrow_s, two_groups, bt, M->wm, M->wmb, stage, lane);
-            }
+            unsigned char *stage = skip_isl ? nullptr : out0 + (size_t)o * stage_bytes;
+            for (int it = cw; it < n_steps; it += kPipeNCompute)
+                sum_pass_step(a, T, slot_s, it, NBT, M->abyte, M->blocksum, sarr(m), stage, lane);
             __syncwarp();
             if (lane == 0) {
+                mbar_arrive(bars + kBarBits + m);
                 mbar_arrive(bars + kBarInEmpty + s);
                 mbar_arrive(bars + kBarOutFull + o);
-                if (cw == 0) trace_stamp(a, T.tile, 7);
+                if (cw == 0) {
+                    trace_stamp(a, T.tile, 3);
+                    trace_stamp(a, T.tile, 7);
+                }
             }
         }
     } else if (warp == kPipeBits) {
@@ -566,7 +547,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(const __grid_
                 }
                 break;
             }
-            const Agg agg = tile_bits<TW>(a, T, M->abyte, words(m), lane);
+            const Agg agg = tile_bits<TW>(a, T, M->abyte, words(m), M->rowtab, lane);
             if (lane == 0) {
                 trace_stamp(a, T.tile, 4);
                 M->agg = agg;
@@ -633,7 +614,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(const __grid_
             if (!pipe_wait(a, bars + kBarOutFull + o, (uint32_t)((i / kNOut) & 1))) break;
             if (gt == 0) trace_stamp(a, T.tile, 12);
             if (!excl.poison && !skip_isl) {
-                copy_out(a, out0 + (size_t)o * stage_bytes, excl, agg, gt, nthr);
+                copy_out(a, out0 + (size_t)o * stage_bytes, M->rowtab, excl, agg, gt, nthr);
                 if (gt == 0) trace_stamp(a, T.tile, 13);
                 if (warp == kPipeWriter0) write_headers<TW>(a, T, words(m), excl, lane);
             }
@@ -651,7 +632,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(const __grid_
 // ============================================================================ host side
 static size_t plain_smem_bytes(int tw, int X, int slot_bytes, int rs, int need_sarr)
 {
-    size_t b = (size_t)slot_bytes + rs;
+    size_t b = (size_t)slot_bytes + (size_t)tw * 2;  // tile slot, row table
     b += (size_t)(((tw * stage_row_bytes(X) + 32) + 15) & ~15);
     b += 128;
     b += (size_t)(tw / 8) * 4;

@@ -93,8 +93,9 @@ struct KArgs {
     int32_t hl, hr, ew, rs;  // halo left/right, extended width, smem row pitch (bytes) = 2 boxw
     int32_t boxw, nbox, box_stride, slot_bytes;
     int32_t use_tma;
-    // stage rows: pitch srow bytes; for even n_xtal, wpr words of data per row
-    // and a pitch of srow/4 words = 4 (mod 8), so staging stores are conflict-free
+    // stage rows: pitch srow bytes = P words, P the first odd number >= ceil(n_xtal/2)
+    // (odd, so that the two rows a warp's staging store writes fall in 2-way
+    // conflicts at worst); for even n_xtal, wpr = n_xtal/2 words of data per row
     int32_t srow, wpr;
     unsigned long long wpr_mul;  // floor(2^32 / wpr) + 1, for w / wpr (w < 2^16)
     int32_t need_sarr;
@@ -185,65 +186,81 @@ __device__ bool decode_tile(const KArgs &a, long long tile, TileInfo &T, const l
 }
 
 // --------------------------------------------------------------------------- crystal sum + threshold
-// Shared-memory address of crystal x's 16 bytes at 8-sample block b of a tile
-// slot; crystals past n_xtal read a zero row.
-__device__ __forceinline__ uint32_t blk_addr(const KArgs &a, uint32_t slot_s, uint32_t zrow_s, int x, int b)
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr)
 {
-    const int c = 8 * b;
-    const int k = (c >= a.boxw) + (c >= 2 * a.boxw) + (c >= 3 * a.boxw) + (c >= 4 * a.boxw);  // nbox <= 5
-    const int col = c - k * a.boxw;
-    if (x >= a.n_xtal) return zrow_s + 2u * (uint32_t)col;
-    return slot_s + (uint32_t)(k * a.box_stride + x * a.rs + 2 * col);
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
 }
 
-// Two 8-sample blocks at once (b1 < 0: only b0), warp-wide: crystal sums,
-// threshold bits and block sums.  Lane L of the ldmatrix transposes holds
-// crystals 8g + 2(L%4), +1 at sample L/4 of a block; dp2a adds both halves and
-// two shuffles finish the crystal sum.  Both blocks' loads are issued first.
-__device__ __forceinline__ void sum_block2(const KArgs &a, const TileInfo &T, uint32_t slot_s, uint32_t zrow_s,
-                                           bool two_groups, int b0, int b1, int nbt, uint8_t *abyte,
-                                           int32_t *blocksum, int32_t *sarr, int lane)
+// Spread the 32 bits of x to the even bit positions of a 64-bit word.
+__device__ __forceinline__ unsigned long long spread_bits(uint32_t x)
 {
-    uint32_t r[2][8];
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int k = 0; k < 8; ++k) r[u][k] = 0u;
-    ldsm_x4_trans(blk_addr(a, slot_s, zrow_s, lane, b0), r[0][0], r[0][1], r[0][2], r[0][3]);
-    if (two_groups) ldsm_x4_trans(blk_addr(a, slot_s, zrow_s, lane + 32, b0), r[0][4], r[0][5], r[0][6], r[0][7]);
-    if (b1 >= 0) {
-        ldsm_x4_trans(blk_addr(a, slot_s, zrow_s, lane, b1), r[1][0], r[1][1], r[1][2], r[1][3]);
-        if (two_groups)
-            ldsm_x4_trans(blk_addr(a, slot_s, zrow_s, lane + 32, b1), r[1][4], r[1][5], r[1][6], r[1][7]);
-    }
-    const int j = lane >> 2;
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const int b = u == 0 ? b0 : b1;
-        if (b < 0) break;
-        int acc = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc = __dp2a_lo((int)r[u][k], 0x0101, acc);
-        acc += __shfl_xor_sync(kFull, acc, 1);
-        acc += __shfl_xor_sync(kFull, acc, 2);
-        const long long t = T.t0 - a.hl + 8 * b + j;
-        const int S = acc - T.ptot;
-        const bool cross = (t >= 0) && (t < T.len) && (S > a.threshold);
-        uint32_t v = __ballot_sync(kFull, cross) & 0x11111111u;
-        v = (v | (v >> 3)) & 0x03030303u;
-        v = (v | (v >> 6)) & 0x000f000fu;
-        v = (v | (v >> 12)) & 0xffu;
-        if (lane == 0) abyte[b] = (uint8_t)v;
-        const int bt = b - a.hl / 8;
-        if (bt >= 0 && bt < nbt) {
-            const bool in = t < T.t_end;
-            int sv = in ? S : 0;
-            sv += __shfl_xor_sync(kFull, sv, 4);
-            sv += __shfl_xor_sync(kFull, sv, 8);
-            sv += __shfl_xor_sync(kFull, sv, 16);
-            if (lane == 0) blocksum[bt] = sv;
-            if (a.need_sarr && (lane & 3) == 0 && in) sarr[8 * bt + j] = S;
+    unsigned long long v = x;
+    v = (v | (v << 16)) & 0x0000ffff0000ffffull;
+    v = (v | (v << 8)) & 0x00ff00ff00ff00ffull;
+    v = (v | (v << 4)) & 0x0f0f0f0f0f0f0f0full;
+    v = (v | (v << 2)) & 0x3333333333333333ull;
+    v = (v | (v << 1)) & 0x5555555555555555ull;
+    return v;
+}
+
+// One warp step of the sum pass over 64 extended columns [64 it, 64 it + 64):
+// lane L owns the two samples of columns c = 64 it + 2L, c + 1, reads their
+// word from every crystal row (conflict-free 4-byte loads) and
+//   - adds the crystals (dp2a takes each 16-bit half with its sign),
+//   - subtracts the summed pedestals and tests the threshold (two ballots give
+//     the 64 threshold bits of the step),
+//   - adds block sums of 8 samples for the Q histograms,
+//   - writes the samples' rows, crystals in order, to the stage area (row =
+//     sample - t0, pitch srow), for samples of the tile proper; two byte
+//     permutes turn (crystal x, x+1) x (sample t, t+1) into row words.
+__device__ __forceinline__ void sum_pass_step(const KArgs &a, const TileInfo &T, uint32_t slot_s, int it,
+                                              int nbt, uint8_t *abyte, int32_t *blocksum, int32_t *sarr,
+                                              unsigned char *stage, int lane)
+{
+    const int X = a.n_xtal;
+    const int c = 64 * it + 2 * lane;
+    const bool have = c < a.ew;  // ew is even, so c + 1 < ew too
+    const int k = (c >= a.boxw) + (c >= 2 * a.boxw) + (c >= 3 * a.boxw) + (c >= 4 * a.boxw);
+    const uint32_t base = slot_s + (uint32_t)(k * a.box_stride + 2 * (c - k * a.boxw));
+    const long long t = T.t0 - a.hl + c;
+    const bool st0 = stage && have && t >= T.t0 && t < T.t_end;
+    const bool st1 = stage && have && t + 1 >= T.t0 && t + 1 < T.t_end;
+    uint32_t *row0 = reinterpret_cast<uint32_t *>(stage + (st0 || st1 ? (t - T.t0) * a.srow : 0));
+    uint32_t *row1 = row0 + (a.srow >> 2);
+    int acc0 = 0, acc1 = 0;
+    if (have) {
+#pragma unroll 3
+        for (int x = 0; x < X; x += 2) {
+            const uint32_t w0 = lds_u32(base + (uint32_t)(x * a.rs));
+            const uint32_t w1 = x + 1 < X ? lds_u32(base + (uint32_t)((x + 1) * a.rs)) : 0u;
+            acc0 = __dp2a_lo((int)w0, 0x0001, acc0);
+            acc1 = __dp2a_lo((int)w0, 0x0100, acc1);
+            acc0 = __dp2a_lo((int)w1, 0x0001, acc0);
+            acc1 = __dp2a_lo((int)w1, 0x0100, acc1);
+            if (st0) row0[x >> 1] = __byte_perm(w0, w1, 0x5410);
+            if (st1) row1[x >> 1] = __byte_perm(w0, w1, 0x7632);
         }
+    }
+    const int S0 = acc0 - T.ptot, S1 = acc1 - T.ptot;
+    const bool in0 = have && t >= 0 && t < T.len, in1 = have && t + 1 >= 0 && t + 1 < T.len;
+    const uint32_t be = __ballot_sync(kFull, in0 && S0 > a.threshold);
+    const uint32_t bo = __ballot_sync(kFull, in1 && S1 > a.threshold);
+    if (lane == 0) {
+        const unsigned long long m = spread_bits(be) | (spread_bits(bo) << 1);
+        *reinterpret_cast<uint2 *>(abyte + 8 * it) = make_uint2((uint32_t)m, (uint32_t)(m >> 32));
+    }
+    // block sums of the tile proper: blocks of 8 samples = 4 lanes
+    const int cp = c - a.hl;  // column within the tile proper
+    const bool proper = have && cp >= 0 && cp < 8 * nbt;
+    int sv = (proper && t < T.t_end ? S0 : 0) + (proper && t + 1 < T.t_end ? S1 : 0);
+    sv += __shfl_xor_sync(kFull, sv, 1);
+    sv += __shfl_xor_sync(kFull, sv, 2);
+    if (proper && (lane & 3) == 0) blocksum[cp >> 3] = sv;
+    if (a.need_sarr && proper) {
+        if (t < T.t_end) sarr[cp] = S0;
+        if (t + 1 < T.t_end) sarr[cp + 1] = S1;
     }
 }
 
@@ -329,7 +346,7 @@ __device__ __forceinline__ uint32_t marks_word(const KArgs &a, uint32_t A, int l
 // word, and the tile's aggregate for the cross-tile scan.
 template <int TW>
 __device__ __forceinline__ Agg tile_bits(const KArgs &a, const TileInfo &T, const uint8_t *abyte, TileWords w,
-                                         int lane)
+                                         int16_t *rowtab, int lane)
 {
     constexpr int NWT = TW / 32;
     const int HL = a.hl;
@@ -383,6 +400,14 @@ __device__ __forceinline__ Agg tile_bits(const KArgs &a, const TileInfo &T, cons
         w.mb[lane] = (int)(excl & 0xffffu);
         w.sb[lane] = (int)(excl >> 16);
         w.ls[lane] = ls;
+        // marked sample of each stage row: row mb + j holds the j-th marked bit
+        uint32_t mm = Mt;
+        int r = (int)(excl & 0xffffu);
+        while (mm) {
+            const int bit = __ffs(mm) - 1;
+            mm &= mm - 1u;
+            rowtab[r++] = (int16_t)(32 * lane + bit);
+        }
     }
     Agg agg;
     agg.m = tot & 0xffffu;
@@ -520,94 +545,51 @@ __device__ Agg look_back(const KArgs &a, long long tile, int lane, unsigned *sta
     }
 }
 
-// --------------------------------------------------------------------------- staging of pool rows
-// Block bt of the tile proper (warp-wide): every marked sample's n_xtal raw
-// values go to its row in the tile-local stage area (row = marked samples
-// before it in the tile).
-__device__ __forceinline__ void stage_block(const KArgs &a, uint32_t slot_s, uint32_t zrow_s, bool two_groups,
-                                            int bt, const uint32_t *w_m, const int32_t *w_mb, unsigned char *stage,
-                                            int lane)
-{
-    const int X = a.n_xtal;
-    const int w = bt >> 2, shift = (bt & 3) * 8;
-    const uint32_t mw = w_m[w];
-    const uint32_t bits = (mw >> shift) & 0xffu;
-    if (!bits) return;
-    const int b = bt + a.hl / 8;
-    uint32_t r[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-    ldsm_x4_trans(blk_addr(a, slot_s, zrow_s, lane, b), r[0], r[1], r[2], r[3]);
-    if (two_groups) ldsm_x4_trans(blk_addr(a, slot_s, zrow_s, lane + 32, b), r[4], r[5], r[6], r[7]);
-    const int j = lane >> 2, q4 = lane & 3;
-    if (!((bits >> j) & 1u)) return;
-    const int rl = w_mb[w] + __popc(mw & ((1u << (shift + j)) - 1u));
-    unsigned char *dst = stage + (size_t)rl * a.srow;
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-        const int x = 8 * g + 2 * q4;
-        if ((g >= 4 && !two_groups) || x >= X) continue;
-        if (x + 1 < X && !(X & 1)) {
-            *reinterpret_cast<uint32_t *>(dst + 2 * x) = r[g];
-        } else {
-            *reinterpret_cast<uint16_t *>(dst + 2 * x) = (uint16_t)(r[g] & 0xffffu);
-            if (x + 1 < X) *reinterpret_cast<uint16_t *>(dst + 2 * x + 2) = (uint16_t)(r[g] >> 16);
-        }
-    }
-}
-
 // --------------------------------------------------------------------------- pool rows to global
-// 16 bytes starting e bytes (even, < 16) into the 32 bytes at p (16-aligned).
-__device__ __forceinline__ uint4 shifted_chunk(const unsigned char *p, int e)
+// The stage area holds every sample row of the tile (row = sample - t0, pitch
+// srow bytes).  Output row r of the tile is stage row rowtab[r].  Output goes
+// to global rows [excl.m, excl.m + agg.m): whole 16-byte chunks from one
+// thread each, the unaligned ends in smaller stores.
+__device__ __forceinline__ void copy_out(const KArgs &a, const unsigned char *stage, const int16_t *rowtab,
+                                         const Agg &excl, const Agg &agg, int gt, int nthr)
 {
-    const uint4 w0 = *reinterpret_cast<const uint4 *>(p);
-    if (e == 0) return w0;
-    const uint4 w1 = *reinterpret_cast<const uint4 *>(p + 16);
-    uint32_t s0, s1, s2, s3, s4;
-    switch (e >> 2) {
-    case 0: s0 = w0.x; s1 = w0.y; s2 = w0.z; s3 = w0.w; s4 = w1.x; break;
-    case 1: s0 = w0.y; s1 = w0.z; s2 = w0.w; s3 = w1.x; s4 = w1.y; break;
-    case 2: s0 = w0.z; s1 = w0.w; s2 = w1.x; s3 = w1.y; s4 = w1.z; break;
-    default: s0 = w0.w; s1 = w1.x; s2 = w1.y; s3 = w1.z; s4 = w1.w; break;
+    long long rows = agg.m;
+    if (excl.m + rows > a.pool_cap) {
+        rows = a.pool_cap - excl.m;
+        if (gt == 0) set_status_bit(a, DAQ_DEV_POOL_OVERFLOW);
     }
-    if (e & 2)
-        return make_uint4(__funnelshift_r(s0, s1, 16), __funnelshift_r(s1, s2, 16), __funnelshift_r(s2, s3, 16),
-                          __funnelshift_r(s3, s4, 16));
-    return make_uint4(s0, s1, s2, s3);
-}
-
-// Rows [excl.m, excl.m + agg.m) from the stage area (a group of nthr threads,
-// id gt).  The body goes out in aligned 16-byte stores; the head and tail
-// (< 16 bytes each, shared with neighbouring tiles' rows) in 2-byte stores.
-// Even n_xtal: rows are wpr words; stage row r holds them at word r * P (P =
-// srow / 4), so output word w comes from stage word (w / wpr) * P + w % wpr.
-__device__ __forceinline__ void copy_out_words(const KArgs &a, const unsigned char *stage, const Agg &excl,
-                                               const Agg &agg, int gt, int nthr)
-{
+    if (rows <= 0) return;
+    if (a.n_xtal & 1) {
+        // odd crystal count: rows are not whole words; one int16 at a time
+        const int X = a.n_xtal, sp = a.srow >> 1;
+        const int16_t *s16 = reinterpret_cast<const int16_t *>(stage);
+        int16_t *g16 = a.pool + excl.m * X;
+        for (long long e = gt; e < rows * X; e += nthr) {
+            const int r = (int)(e / X), x = (int)(e - (long long)r * X);
+            g16[e] = s16[rowtab[r] * sp + x];
+        }
+        return;
+    }
     const uint32_t *sw = reinterpret_cast<const uint32_t *>(stage);
     const int P = a.srow >> 2, wpr = a.wpr;
     const long long G0 = excl.m * wpr;  // global word of the tile's first output word
-    long long n_words = agg.m * wpr;
-    const long long cap_w = a.pool_cap * wpr;
-    if (G0 + n_words > cap_w) {
-        n_words = cap_w - G0;
-        if (gt == 0) set_status_bit(a, DAQ_DEV_POOL_OVERFLOW);
-    }
-    if (n_words <= 0) return;
+    const long long n_words = rows * wpr;
     uint32_t *g32 = reinterpret_cast<uint32_t *>(a.pool) + G0;
     auto row_of = [&](uint32_t w) {
         uint32_t r = (uint32_t)(((unsigned long long)w * a.wpr_mul) >> 32);
         if (r * (uint32_t)wpr > w) --r;
         return r;
     };
-    auto src = [&](uint32_t w) {
+    auto src_word = [&](uint32_t w) {
         const uint32_t r = row_of(w);
-        return r * (uint32_t)P + (w - r * (uint32_t)wpr);
+        return (uint32_t)rowtab[r] * (uint32_t)P + (w - r * (uint32_t)wpr);
     };
     const int head = (int)min((long long)((4 - (G0 & 3)) & 3), n_words);
     const long long n_chunks = (n_words - head) >> 2;
     const long long tail0 = head + 4 * n_chunks;
     const int n_tail = (int)(n_words - tail0);
-    if (gt < head) g32[gt] = sw[src((uint32_t)gt)];
-    else if (gt >= 4 && gt < 4 + n_tail) g32[tail0 + gt - 4] = sw[src((uint32_t)(tail0 + gt - 4))];
+    if (gt < head) g32[gt] = sw[src_word((uint32_t)gt)];
+    else if (gt >= 4 && gt < 4 + n_tail) g32[tail0 + gt - 4] = sw[src_word((uint32_t)(tail0 + gt - 4))];
     constexpr int U = 4;
     for (long long c0 = gt; c0 < n_chunks; c0 += (long long)U * nthr) {
         uint4 out[U];
@@ -617,15 +599,17 @@ __device__ __forceinline__ void copy_out_words(const KArgs &a, const unsigned ch
             out[u] = make_uint4(0u, 0u, 0u, 0u);
             if (c < n_chunks) {
                 const uint32_t w = (uint32_t)(head + 4 * c);
-                const uint32_t r = row_of(w);
-                uint32_t k = w - r * (uint32_t)wpr, base = r * (uint32_t)P;
+                uint32_t r = row_of(w);
+                uint32_t k = w - r * (uint32_t)wpr;
+                uint32_t base = (uint32_t)rowtab[r] * (uint32_t)P;
                 uint32_t vals[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     vals[e] = sw[base + k];
-                    if (++k == (uint32_t)wpr) {
+                    if (++k == (uint32_t)wpr && e < 3) {
                         k = 0;
-                        base += P;
+                        ++r;
+                        base = (uint32_t)rowtab[r] * (uint32_t)P;
                     }
                 }
                 out[u] = make_uint4(vals[0], vals[1], vals[2], vals[3]);
@@ -635,51 +619,6 @@ __device__ __forceinline__ void copy_out_words(const KArgs &a, const unsigned ch
         for (int u = 0; u < U; ++u) {
             const long long c = c0 + (long long)u * nthr;
             if (c < n_chunks) st_global_cs_v4(g32 + head + 4 * c, out[u].x, out[u].y, out[u].z, out[u].w);
-        }
-    }
-}
-
-__device__ __forceinline__ void copy_out(const KArgs &a, const unsigned char *stage, const Agg &excl,
-                                         const Agg &agg, int gt, int nthr)
-{
-    if (!(a.n_xtal & 1)) {
-        copy_out_words(a, stage, excl, agg, gt, nthr);
-        return;
-    }
-    const long long rb = 2ll * a.n_xtal;
-    const long long cap_b = a.pool_cap * rb;
-    const long long gs = excl.m * rb;
-    long long ge = gs + agg.m * rb;
-    if (ge > cap_b) {
-        ge = cap_b;
-        if (gt == 0) set_status_bit(a, DAQ_DEV_POOL_OVERFLOW);
-    }
-    if (ge <= gs) return;
-    unsigned char *g = reinterpret_cast<unsigned char *>(a.pool);
-    long long a16 = (gs + 15) & ~15ll, b16 = ge & ~15ll;
-    if (a16 > ge) a16 = ge;
-    if (b16 < a16) b16 = a16;
-    const int n_head = (int)((a16 - gs) >> 1), n_tail = (int)((ge - b16) >> 1);
-    if (gt < n_head)
-        *reinterpret_cast<uint16_t *>(g + gs + 2 * gt) = *reinterpret_cast<const uint16_t *>(stage + 2 * gt);
-    else if (gt >= 8 && gt < 8 + n_tail) {
-        const long long o = b16 + 2 * (gt - 8);
-        *reinterpret_cast<uint16_t *>(g + o) = *reinterpret_cast<const uint16_t *>(stage + (o - gs));
-    }
-    const int e = (int)(a16 - gs);  // stage offset of global a16: even, < 16
-    const long long n_chunks = (b16 - a16) >> 4;
-    constexpr int U = 4;  // chunks per thread per round: loads first, then stores
-    for (long long i0 = gt; i0 < n_chunks; i0 += (long long)U * nthr) {
-        uint4 out[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const long long i = i0 + (long long)u * nthr;
-            if (i < n_chunks) out[u] = shifted_chunk(stage + 16 * i, e);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const long long i = i0 + (long long)u * nthr;
-            if (i < n_chunks) st_global_cs_v4(g + a16 + 16 * i, out[u].x, out[u].y, out[u].z, out[u].w);
         }
     }
 }
