@@ -64,6 +64,7 @@ def main():
     ap.add_argument("--calos", type=int, default=24)
     ap.add_argument("--grid", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--flags", type=int, default=0, help="daq_params.flags (1 = skip Q, 2 = skip islands)")
     ap.add_argument("--out", default=None, help="save the raw trace (.npy)")
     args = ap.parse_args()
     w = W.scaled(W.PLAIN_FULL_FILL, n_calo=args.calos)
@@ -72,11 +73,12 @@ def main():
     p = daq.make_params(**w.params(), tile=args.tile, grid=args.grid)
     n_tiles = daq.daq_trace_tiles(C, X, N, F, p)
     trace = torch.zeros((n_tiles, DAQ_TRACE_WORDS), dtype=torch.int64, device="cuda")
-    res = daq.process_fills(s, tile=args.tile, grid=args.grid, **w.params())   # warm-up
+    res = daq.process_fills(s, tile=args.tile, grid=args.grid, flags=args.flags, **w.params())   # warm-up
     outs, ws = res["outputs"], res["workspace"]
     for _ in range(3):
-        daq.process_fills(s, tile=args.tile, grid=args.grid, outputs=outs, workspace=ws, **w.params())
-    p = daq.make_params(**w.params(), tile=args.tile, grid=args.grid,
+        daq.process_fills(s, tile=args.tile, grid=args.grid, outputs=outs, workspace=ws, flags=args.flags,
+                          **w.params())
+    p = daq.make_params(**w.params(), tile=args.tile, grid=args.grid, flags=args.flags,
                         stream=torch.cuda.current_stream())
     p.workspace, p.workspace_bytes = ws.data_ptr(), ws.numel()
     p.trace = trace.data_ptr()
@@ -88,7 +90,7 @@ def main():
     if args.out:
         np.save(args.out, tr)
     summary = summarize(tr)
-    summary.update(grid=args.grid, tile=args.tile, calos=args.calos)
+    summary.update(grid=args.grid, tile=args.tile, calos=args.calos, flags=args.flags)
     print(json.dumps(summary, indent=1))
 
 
