@@ -86,17 +86,20 @@ typedef struct daq_island {
  *   tile         largest samples per tile to use: 0 = 448; else 128, 224, 448 or
  *                960.  The call takes the largest supported width not above it
  *                whose shared-memory plan fits (960 only for the plain kernel).
- *   grid         0  = pipelined persistent kernel, one CTA per SM (default);
- *                > 0 = pipelined kernel with exactly this many CTAs;
- *                -1 = plain kernel, one CTA per tile (non-persistent form);
- *                -2 = plain kernel, persistent (resident CTAs per SM x SMs).
+ *   grid         0  = two-pass form (count kernel, scan, compact kernel), grids
+ *                     from occupancy (default);
+ *                > 0 = two-pass form with exactly this many CTAs per kernel;
+ *                -1 = single-pass plain kernel, one CTA per tile;
+ *                -2 = single-pass plain kernel, persistent;
+ *                -3 = single-pass pipelined kernel (one CTA per SM, warp roles).
  *   stream       cudaStream_t (NULL = legacy default stream).
  *   workspace    device scratch of at least daq_workspace_size() bytes,
  *                16-byte aligned; reused by the call and not to be shared by
  *                calls that may run at the same time.
- *   events       NULL, or a host array of three cudaEvent_t that the call
- *                records on `stream` before the pedestal kernel, between the
- *                two kernels and after the tile kernel (per-kernel timing).
+ *   events       NULL, or a host array of DAQ_N_EVENTS cudaEvent_t that the call
+ *                records on `stream`: [0] start, [1] after the pedestal kernel,
+ *                [2] after the count (single-pass: tile) kernel, [3] after the
+ *                scan, [4] end (per-kernel timing).
  *   trace        NULL, or device uint64[max_tiles][DAQ_TRACE_WORDS] (max_tiles
  *                from daq_trace_tiles()): per-tile %globaltimer stamps of each
  *                stage (profiling only; costs a few stores per tile).
@@ -120,6 +123,8 @@ typedef struct daq_params {
     void *const *events;
     uint64_t *trace;
 } daq_params;
+
+#define DAQ_N_EVENTS 5
 
 /* Per-tile trace record: stamps in nanoseconds (%globaltimer), 0 = stage not reached.
  * [0] ticket taken  [1] load issued  [2] load landed  [3] sums done  [4] marks done

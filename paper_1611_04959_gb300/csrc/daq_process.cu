@@ -43,6 +43,7 @@
 #include "daq.h"
 #include "daq_device.cuh"
 #include "daq_steps.cuh"
+#include "daq_twopass.cuh"
 
 namespace daq {
 
@@ -61,7 +62,7 @@ static int stage_row_bytes(int X)
 
 // Workspace layout (byte offsets from the workspace base).
 struct WsLayout {
-    size_t ticket, fts, lens, ptot, status, total;
+    size_t ticket, fts, lens, ptot, status, marks, recs, excl, blockagg, total;
 };
 
 static WsLayout ws_layout(int64_t n_fills, int64_t n_calo, int64_t max_tiles)
@@ -73,7 +74,12 @@ static WsLayout ws_layout(int64_t n_fills, int64_t n_calo, int64_t max_tiles)
     w.lens = up(w.fts + sizeof(long long) * (size_t)(n_fills + 1));
     w.ptot = up(w.lens + sizeof(int32_t) * (size_t)(n_fills > 0 ? n_fills : 1));
     w.status = up(w.ptot + sizeof(int32_t) * (size_t)(n_fills * n_calo > 0 ? n_fills * n_calo : 1));
-    w.total = up(w.status + sizeof(TileStatus) * (size_t)(max_tiles > 0 ? max_tiles : 1));
+    const size_t nt = (size_t)(max_tiles > 0 ? max_tiles : 1);
+    w.marks = up(w.status + sizeof(TileStatus) * nt);
+    w.recs = up(w.marks + sizeof(uint32_t) * (size_t)(kMaxTileWords) * nt);
+    w.excl = up(w.recs + sizeof(TileRec) * nt);
+    w.blockagg = up(w.excl + sizeof(TileExcl) * nt);
+    w.total = up(w.blockagg + sizeof(Agg) * ((nt + kScanChunk - 1) / kScanChunk));
     return w;
 }
 
@@ -95,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) daq_prepare_kernel(KArgs a, int tw)
     __shared__ long long s_carry;
     __shared__ long long s_ped[kWarps];
 
-    {
+    if (a.mode != kModeTwoPass) {  // scan state of the single-pass kernels
         uint4 *st = reinterpret_cast<uint4 *>(a.status);
         const long long n16 = a.max_tiles * (long long)(sizeof(TileStatus) / 16);
         for (long long i = (long long)blockIdx.x * kThreads + tid; i < n16; i += (long long)gridDim.x * kThreads)
@@ -170,38 +176,6 @@ __global__ void __launch_bounds__(kThreads) daq_prepare_kernel(KArgs a, int tw)
             a.ptot[cf] = (int32_t)t;
         }
         __syncthreads();
-    }
-}
-
-// Issue the TMA box loads of one tile (one thread; the caller armed `bar`).
-__device__ __forceinline__ void issue_tile_load(const KArgs &a, const TileInfo &T, unsigned char *slot,
-                                                uint64_t *bar)
-{
-    const int c0 = (int)(T.t0 - a.hl);
-    const int c1 = (int)(((long long)T.f * a.n_calo + T.c) * a.n_xtal);
-    for (int k = 0; k < a.nbox; ++k) tma_load_2d(slot + (size_t)k * a.box_stride, &a.tmap, c0 + k * a.boxw, c1, bar);
-}
-
-__device__ __forceinline__ uint32_t tile_load_bytes(const KArgs &a)
-{
-    return (uint32_t)a.nbox * (uint32_t)a.n_xtal * (uint32_t)a.rs;
-}
-
-// Fallback load with plain loads (rows not 16-byte aligned), same layout as the boxes.
-__device__ __forceinline__ void plain_tile_load(const KArgs &a, const TileInfo &T, unsigned char *slot, int tid,
-                                                int nthr)
-{
-    const int X = a.n_xtal, W = a.nbox * a.boxw;
-    const long long e0 = T.t0 - a.hl;
-    const long long cf = (long long)T.f * a.n_calo + T.c;
-    const int16_t *rows = a.samples + cf * X * a.n_samples;
-    for (int i = tid; i < X * W; i += nthr) {
-        const int x = i / W, c = i - x * W;
-        const int k = c / a.boxw, col = c - k * a.boxw;
-        const long long t = e0 + c;
-        int16_t v = 0;
-        if (t >= 0 && t < a.n_samples) v = rows[(long long)x * a.n_samples + t];
-        *reinterpret_cast<int16_t *>(slot + (size_t)k * a.box_stride + (size_t)x * a.rs + 2 * col) = v;
     }
 }
 
@@ -675,10 +649,36 @@ static DeviceInfo device_info(int dev)
 constexpr int kSmemBudget = 227 * 1024;
 
 struct Plan {
-    int tw, hl, hr, ew, rs, boxw, nbox, box_stride, slot_bytes, need_sarr, pipelined;
-    size_t smem;
+    int tw, hl, hr, ew, rs, boxw, nbox, box_stride, slot_bytes, need_sarr, mode;
+    int boxw_b, nbox_b, box_stride_b, slot_bytes_b, rs_b;  // compact pass (two-pass mode)
+    size_t smem, smem_b;                                   // tile (or count) kernel, compact kernel
     int64_t max_tiles;
 };
+
+// Box geometry of `width` samples: nbox boxes of boxw <= 248 samples, boxw an
+// odd multiple of 8 (box rows are then an odd multiple of 16 bytes).
+static void box_geometry(int width, int X, int *nbox, int *boxw, int *box_stride)
+{
+    *nbox = (width + 247) / 248;
+    int bw = (((width + *nbox - 1) / *nbox) + 7) & ~7;
+    if (((bw / 8) & 1) == 0) bw += 8;
+    *boxw = bw;
+    *box_stride = (X * 2 * bw + 127) & ~127;
+}
+
+static size_t count_smem_bytes(int tw, int slot_bytes, int need_sarr)
+{
+    size_t b = 2 * (size_t)slot_bytes + 128 + (size_t)(tw / 8) * 4 + (need_sarr ? (size_t)tw * 4 : 0);
+    b += 16 + 2 * sizeof(TileInfo) + 2 * 8;
+    return (b + 127) & ~size_t(127);
+}
+
+static size_t compact_smem_bytes(int tw, int X, int slot_bytes_b)
+{
+    size_t b = (size_t)slot_bytes_b + (size_t)(((tw * 2 * X + 32) + 15) & ~15) + (size_t)(tw / 32) * 4 * 6;
+    b += 16 + sizeof(TileInfo) + 2 * sizeof(Agg) + 8;
+    return (b + 127) & ~size_t(127);
+}
 
 // Extended tile = nbox TMA boxes of boxw samples: boxw <= 248 and an odd
 // multiple of 8, so a box row (2 boxw bytes) is an odd multiple of 16 bytes.
@@ -695,8 +695,18 @@ static void plan_geometry(Plan *pl, int tw, int pre, int post, int X)
     pl->rs = 2 * boxw;
     pl->box_stride = (X * pl->rs + 127) & ~127;
     pl->slot_bytes = pl->nbox * pl->box_stride;
-    pl->smem = pl->pipelined ? pipe_smem(tw, X, pl->slot_bytes, pl->rs, pl->need_sarr)
-                             : plain_smem_bytes(tw, X, pl->slot_bytes, pl->rs, pl->need_sarr);
+    box_geometry(tw, X, &pl->nbox_b, &pl->boxw_b, &pl->box_stride_b);
+    pl->rs_b = 2 * pl->boxw_b;
+    pl->slot_bytes_b = pl->nbox_b * pl->box_stride_b;
+    pl->smem_b = 0;
+    if (pl->mode == kModePipelined) {
+        pl->smem = pipe_smem(tw, X, pl->slot_bytes, pl->rs, pl->need_sarr);
+    } else if (pl->mode == kModePlain) {
+        pl->smem = plain_smem_bytes(tw, X, pl->slot_bytes, pl->rs, pl->need_sarr);
+    } else {
+        pl->smem = count_smem_bytes(tw, pl->slot_bytes, pl->need_sarr);
+        pl->smem_b = compact_smem_bytes(tw, X, pl->slot_bytes_b);
+    }
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
@@ -736,7 +746,7 @@ static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, con
     if (n_xtal > kMaxXtal) return DAQ_EUNSUPPORTED;
     if (p->pre < 0 || p->post < 0 || p->pre + p->post > 512 || p->ped_samples < 1) return DAQ_EINVAL;
     if (p->n_decim < 0 || p->n_decim > 2) return DAQ_EINVAL;
-    if (p->grid < -2) return DAQ_EINVAL;
+    if (p->grid < -3) return DAQ_EINVAL;
     // scan fields: trailing run < 2^30 samples, island count < 2^31
     if (n_samples > ((int64_t)1 << 30) || (int64_t)n_fills * n_calo * n_samples > ((int64_t)1 << 32))
         return DAQ_EUNSUPPORTED;
@@ -746,16 +756,16 @@ static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, con
         if (p->decim[d] % 8) pl->need_sarr = 1;
     }
     if (p->tile != 0 && p->tile != 128 && p->tile != 224 && p->tile != 448 && p->tile != 960) return DAQ_EINVAL;
-    pl->pipelined = p->grid >= 0;
+    pl->mode = p->grid >= 0 ? kModeTwoPass : (p->grid == -3 ? kModePipelined : kModePlain);
     const int hl = (p->post + 1 + 7) & ~7, hr = (p->pre + 1 + 7) & ~7;
     const int limit = p->tile ? p->tile : 448;
     int chosen = -1;
     for (int tw : {960, 448, 224, 128}) {
         if (tw > limit) continue;
-        if (tw == 960 && pl->pipelined) continue;
+        if (tw == 960 && pl->mode != kModePlain) continue;
         if (tw + hl + hr > kMaxExtBits) continue;
         plan_geometry(pl, tw, p->pre, p->post, n_xtal);
-        if (pl->smem > (size_t)kSmemBudget) continue;
+        if (pl->smem > (size_t)kSmemBudget || pl->smem_b > (size_t)kSmemBudget) continue;
         chosen = tw;
         break;
     }
@@ -803,6 +813,47 @@ template <int TW> static cudaError_t launch_pipe(const KArgs &a, const Plan &pl,
     if (e != cudaSuccess) return e;
     daq_pipe_kernel<TW><<<grid, kPipeThreads, pl.smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// Count pass, scan, compact pass.  Events (optional): [2] after the count
+// kernel, [3] after the scan, [4] after the compact kernel.
+template <int TW>
+static cudaError_t launch_twopass(const KArgs &a, const Plan &pl, int grid, int sms, bool skip_isl,
+                                  cudaEvent_t const *ev, cudaStream_t s)
+{
+    static size_t conf_a[64] = {0}, conf_b[64] = {0};
+    cudaError_t e = ensure_smem(daq_count_kernel<TW>, pl.smem, conf_a);
+    if (e != cudaSuccess) return e;
+    e = ensure_smem(daq_compact_kernel<TW>, pl.smem_b, conf_b);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = std::max<int64_t>(1, pl.max_tiles);
+    int grid_a = grid, grid_b = grid;
+    if (grid <= 0) {
+        int per_a = 0, per_b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_a, daq_count_kernel<TW>, 256, pl.smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_b, daq_compact_kernel<TW>, 256, pl.smem_b);
+        if (e != cudaSuccess) return e;
+        if (per_a < 1 || per_b < 1) return cudaErrorInvalidConfiguration;
+        grid_a = per_a * sms;
+        grid_b = per_b * sms;
+    }
+    grid_a = (int)std::min<int64_t>(grid_a, tiles);
+    grid_b = (int)std::min<int64_t>(grid_b, tiles);
+    daq_count_kernel<TW><<<grid_a, 256, pl.smem, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
+    const int scan_blocks = (int)((tiles + kScanChunk - 1) / kScanChunk);
+    daq_scan_reduce_kernel<<<scan_blocks, kScanThreads, 0, s>>>(a);
+    daq_scan_apply_kernel<<<scan_blocks, kScanThreads, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
+    if (!skip_isl) {
+        daq_compact_kernel<TW><<<grid_b, 256, pl.smem_b, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (ev && (e = cudaEventRecord(ev[4], s)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 static int64_t q_bins(int64_t n, int32_t d) { return d > 0 ? (n + d - 1) / d : 0; }
@@ -894,13 +945,21 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
     a.nbox = pl.nbox;
     a.box_stride = pl.box_stride;
     a.slot_bytes = pl.slot_bytes;
+    a.boxw_b = pl.boxw_b;
+    a.nbox_b = pl.nbox_b;
+    a.box_stride_b = pl.box_stride_b;
+    a.slot_bytes_b = pl.slot_bytes_b;
+    a.rs_b = pl.rs_b;
+    a.mode = pl.mode;
     a.srow = stage_row_bytes(n_xtal);
     a.wpr = n_xtal / 2;
     a.wpr_mul = a.wpr > 0 ? (1ull << 32) / (unsigned long long)a.wpr + 1 : 0ull;
     a.use_tma = 0;
     if (total > 0 && n_samples % 8 == 0 && (reinterpret_cast<uintptr_t>(samples) & 15) == 0)
         a.use_tma = encode_tensor_map(&a.tmap, samples, (int64_t)n_fills * n_calo * n_xtal, n_samples, pl.boxw,
-                                      n_xtal);
+                                      n_xtal) &&
+                    encode_tensor_map(&a.tmap_b, samples, (int64_t)n_fills * n_calo * n_xtal, n_samples,
+                                      pl.boxw_b, n_xtal);
     a.need_sarr = pl.need_sarr;
     a.max_tiles = pl.max_tiles;
     a.hdr = skip_isl ? nullptr : out->hdr;
@@ -916,6 +975,10 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
     a.lens = reinterpret_cast<int32_t *>(ws + wl.lens);
     a.ptot = reinterpret_cast<int32_t *>(ws + wl.ptot);
     a.status = reinterpret_cast<TileStatus *>(ws + wl.status);
+    a.marks = reinterpret_cast<uint32_t *>(ws + wl.marks);
+    a.recs = ws + wl.recs;
+    a.excl = ws + wl.excl;
+    a.blockagg = reinterpret_cast<Agg *>(ws + wl.blockagg);
     a.trace = reinterpret_cast<unsigned long long *>(p.trace);
 
     cudaStream_t s = static_cast<cudaStream_t>(p.stream);
@@ -923,7 +986,7 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
     if (cudaGetDevice(&dev) != cudaSuccess) return DAQ_ECUDA;
     const DeviceInfo di = device_info(dev);
     if (di.sms <= 0) return DAQ_ECUDA;
-    if ((int)pl.smem > di.smem_optin) return DAQ_EUNSUPPORTED;
+    if ((int)pl.smem > di.smem_optin || (int)pl.smem_b > di.smem_optin) return DAQ_EUNSUPPORTED;
 
     cudaEvent_t const *ev = reinterpret_cast<cudaEvent_t const *>(p.events);
     if (ev && cudaEventRecord(ev[0], s) != cudaSuccess) return DAQ_ECUDA;
@@ -935,7 +998,13 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
 
     const int64_t tiles_cap = std::max<int64_t>(1, std::min<int64_t>(pl.max_tiles, INT32_MAX));
     cudaError_t e;
-    if (pl.pipelined) {
+    if (pl.mode == kModeTwoPass) {
+        switch (pl.tw) {
+        case 128: e = launch_twopass<128>(a, pl, p.grid, di.sms, skip_isl, ev, s); break;
+        case 224: e = launch_twopass<224>(a, pl, p.grid, di.sms, skip_isl, ev, s); break;
+        default: e = launch_twopass<448>(a, pl, p.grid, di.sms, skip_isl, ev, s); break;
+        }
+    } else if (pl.mode == kModePipelined) {
         int grid = p.grid > 0 ? p.grid : di.sms;
         grid = (int)std::min<int64_t>(grid, tiles_cap);
         switch (pl.tw) {
@@ -954,7 +1023,9 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
         }
     }
     if (e != cudaSuccess) return DAQ_ECUDA;
-    if (ev && cudaEventRecord(ev[2], s) != cudaSuccess) return DAQ_ECUDA;
+    if (ev && pl.mode != kModeTwoPass)
+        for (int k = 2; k < 5; ++k)
+            if (cudaEventRecord(ev[k], s) != cudaSuccess) return DAQ_ECUDA;
 
     if (p.flags & DAQ_SYNC) {
         if (cudaStreamSynchronize(s) != cudaSuccess) return DAQ_ECUDA;

@@ -20,6 +20,9 @@
 namespace daq {
 
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // bounded device waits (4 s)
+constexpr int kMaxTileWords = 14;                 // marks words of the widest two-pass tile (448 samples)
+// kernels a call may use (daq_params.grid picks one)
+enum : int32_t { kModeTwoPass = 0, kModePlain = 1, kModePipelined = 2 };
 constexpr int kMaxXtal = 64;
 constexpr int kMaxExtBits = 1024;  // tile + halos: one warp of 32-bit words
 
@@ -68,6 +71,17 @@ __device__ __forceinline__ Agg shfl_agg(const Agg &a, int src)
     return r;
 }
 
+__device__ __forceinline__ Agg shfl_up_agg(const Agg &a, int d)
+{
+    Agg r;
+    r.m = __shfl_up_sync(kFull, a.m, d);
+    r.s = __shfl_up_sync(kFull, a.s, d);
+    r.tr = __shfl_up_sync(kFull, a.tr, d);
+    r.full = __shfl_up_sync(kFull, a.full, d);
+    r.poison = __shfl_up_sync(kFull, a.poison, d);
+    return r;
+}
+
 __device__ __forceinline__ Agg shfl_down_agg(const Agg &a, int d)
 {
     Agg r;
@@ -80,7 +94,8 @@ __device__ __forceinline__ Agg shfl_down_agg(const Agg &a, int d)
 }
 
 struct KArgs {
-    CUtensorMap tmap;  // samples as a 2-D tensor [F*C*X rows][n_samples], when use_tma
+    CUtensorMap tmap;    // samples as a 2-D tensor [F*C*X rows][n_samples], when use_tma: boxes with halo
+    CUtensorMap tmap_b;  // the same tensor, boxes of the compact pass (tile proper only)
     const int16_t *samples;
     int32_t n_calo, n_xtal, n_fills;
     int64_t n_samples;  // row pitch
@@ -92,7 +107,9 @@ struct KArgs {
     uint32_t flags;
     int32_t hl, hr, ew, rs;  // halo left/right, extended width, smem row pitch (bytes) = 2 boxw
     int32_t boxw, nbox, box_stride, slot_bytes;
+    int32_t boxw_b, nbox_b, box_stride_b, slot_bytes_b, rs_b;  // compact pass: tile proper only
     int32_t use_tma;
+    int32_t mode;
     // stage rows: pitch srow bytes = P words, P the first odd number >= ceil(n_xtal/2)
     // (odd, so that the two rows a warp's staging store writes fall in 2-way
     // conflicts at worst); for even n_xtal, wpr = n_xtal/2 words of data per row
@@ -114,6 +131,10 @@ struct KArgs {
     int32_t *lens;               // [n_fills], clamped
     int32_t *ptot;               // [n_fills * n_calo]
     TileStatus *status;          // [max_tiles]
+    uint32_t *marks;             // two-pass: [max_tiles][TW/32] marks words of each tile
+    void *recs;                  // two-pass: [max_tiles] tile aggregates
+    void *excl;                  // two-pass: [max_tiles] exclusive prefixes
+    Agg *blockagg;               // two-pass: [scan blocks] aggregates of each scan block
     unsigned long long *trace;   // NULL or [max_tiles][16] stage stamps
 };
 
@@ -183,6 +204,39 @@ __device__ bool decode_tile(const KArgs &a, long long tile, TileInfo &T, const l
     T.ptot = a.ptot[(long long)lo * a.n_calo + T.c];
     T.pad = 0;
     return true;
+}
+
+// --------------------------------------------------------------------------- tile loads
+// Issue the TMA box loads of one tile (one thread; the caller armed `bar`).
+__device__ __forceinline__ void issue_tile_load(const KArgs &a, const TileInfo &T, unsigned char *slot,
+                                                uint64_t *bar)
+{
+    const int c0 = (int)(T.t0 - a.hl);
+    const int c1 = (int)(((long long)T.f * a.n_calo + T.c) * a.n_xtal);
+    for (int k = 0; k < a.nbox; ++k) tma_load_2d(slot + (size_t)k * a.box_stride, &a.tmap, c0 + k * a.boxw, c1, bar);
+}
+
+__device__ __forceinline__ uint32_t tile_load_bytes(const KArgs &a)
+{
+    return (uint32_t)a.nbox * (uint32_t)a.n_xtal * (uint32_t)a.rs;
+}
+
+// Fallback load with plain loads (rows not 16-byte aligned), same layout as the boxes.
+__device__ __forceinline__ void plain_tile_load(const KArgs &a, const TileInfo &T, unsigned char *slot, int tid,
+                                                int nthr)
+{
+    const int X = a.n_xtal, W = a.nbox * a.boxw;
+    const long long e0 = T.t0 - a.hl;
+    const long long cf = (long long)T.f * a.n_calo + T.c;
+    const int16_t *rows = a.samples + cf * X * a.n_samples;
+    for (int i = tid; i < X * W; i += nthr) {
+        const int x = i / W, c = i - x * W;
+        const int k = c / a.boxw, col = c - k * a.boxw;
+        const long long t = e0 + c;
+        int16_t v = 0;
+        if (t >= 0 && t < a.n_samples) v = rows[(long long)x * a.n_samples + t];
+        *reinterpret_cast<int16_t *>(slot + (size_t)k * a.box_stride + (size_t)x * a.rs + 2 * col) = v;
+    }
 }
 
 // --------------------------------------------------------------------------- crystal sum + threshold
@@ -340,31 +394,17 @@ __device__ __forceinline__ uint32_t marks_word(const KArgs &a, uint32_t A, int l
     return Mv;
 }
 
-// --------------------------------------------------------------------------- windows + merge (one warp)
-// From the threshold bits of the extended tile: marks M (crossings widened by
-// pre/post samples), island starts and ends inside the tile, prefix counts per
-// word, and the tile's aggregate for the cross-tile scan.
+// Island structure of the tile proper from its marks (one warp; lane w holds
+// marks word w, bits [32w, 32w + 32) of the tile, 0 past the tile), the marks
+// of the samples just before (m_prev) and after (m_next) the tile, and nt =
+// samples in the tile.  Writes starts, ends, per-word prefix counts and the
+// last island start before each word (TileWords, nullable), optionally the row
+// table (row -> marked sample), and returns the tile's aggregate.
 template <int TW>
-__device__ __forceinline__ Agg tile_bits(const KArgs &a, const TileInfo &T, const uint8_t *abyte, TileWords w,
-                                         int16_t *rowtab, int lane)
+__device__ __forceinline__ Agg words_from_marks(uint32_t Mt, uint32_t m_prev, uint32_t m_next, int nt,
+                                                TileWords w, int16_t *rowtab, int lane)
 {
     constexpr int NWT = TW / 32;
-    const int HL = a.hl;
-    const int NWE = (a.ew + 31) / 32;
-    const long long e0 = T.t0 - HL;
-    const uint32_t A = lane < NWE ? reinterpret_cast<const uint32_t *>(abyte)[lane] : 0u;
-    uint32_t Mv = marks_word(a, A, lane);
-    Mv &= range_mask(32ll * lane, -e0, T.len - e0);  // only samples of [0, len) are marked
-    const uint32_t prev_w = __shfl_sync(kFull, Mv, (HL - 1) >> 5);
-    const uint32_t next_w = __shfl_sync(kFull, Mv, (HL + TW) >> 5);
-    const int qo = HL >> 5, sh = HL & 31;
-    uint32_t lo_w = __shfl_down_sync(kFull, Mv, qo);
-    uint32_t hi_w = __shfl_down_sync(kFull, Mv, qo + 1 < 32 ? qo + 1 : 31);
-    const uint32_t m_prev = (prev_w >> ((HL - 1) & 31)) & 1u;
-    const uint32_t m_next = (next_w >> ((HL + TW) & 31)) & 1u;
-    if (lane + qo > 31) lo_w = 0u;
-    if (lane + qo + 1 > 31) hi_w = 0u;
-    uint32_t Mt = sh ? ((lo_w >> sh) | (hi_w << (32 - sh))) : lo_w;
     if (lane >= NWT) Mt = 0u;
     uint32_t below = __shfl_up_sync(kFull, Mt, 1);
     uint32_t above = __shfl_down_sync(kFull, Mt, 1);
@@ -390,16 +430,17 @@ __device__ __forceinline__ Agg tile_bits(const KArgs &a, const TileInfo &T, cons
     const int ls_incl_prev = __shfl_up_sync(kFull, mx, 1);
     const uint32_t excl = x - packed;
     const int ls = lane == 0 ? -1 : ls_incl_prev;
-    const int nt = (int)(T.t_end - T.t0);
     const uint32_t zeros = ~Mt & range_mask(32ll * lane, 0, nt);
     const int lz = (int)__reduce_max_sync(kFull, zeros ? (unsigned)(32 * lane + 32 - __clz(zeros)) : 0u) - 1;
-    if (lane < NWT) {
+    if (lane < NWT && w.m) {
         w.m[lane] = Mt;
         w.s[lane] = St;
         w.e[lane] = Et;
         w.mb[lane] = (int)(excl & 0xffffu);
         w.sb[lane] = (int)(excl >> 16);
         w.ls[lane] = ls;
+    }
+    if (lane < NWT && rowtab) {
         // marked sample of each stage row: row mb + j holds the j-th marked bit
         uint32_t mm = Mt;
         int r = (int)(excl & 0xffffu);
@@ -416,6 +457,46 @@ __device__ __forceinline__ Agg tile_bits(const KArgs &a, const TileInfo &T, cons
     agg.full = (lz < 0) && m_prev;
     agg.poison = 0;
     return agg;
+}
+
+// Marks of the tile proper from the threshold bits of the extended tile (one
+// warp): returns this lane's marks word of the tile proper and, through
+// *edges, bit 0 = mark of sample t0 - 1 and bit 1 = mark of sample t0 + TW.
+template <int TW>
+__device__ __forceinline__ uint32_t tile_marks(const KArgs &a, const TileInfo &T, const uint8_t *abyte,
+                                               unsigned *edges, int lane)
+{
+    constexpr int NWT = TW / 32;
+    const int HL = a.hl;
+    const int NWE = (a.ew + 31) / 32;
+    const long long e0 = T.t0 - HL;
+    const uint32_t A = lane < NWE ? reinterpret_cast<const uint32_t *>(abyte)[lane] : 0u;
+    uint32_t Mv = marks_word(a, A, lane);
+    Mv &= range_mask(32ll * lane, -e0, T.len - e0);  // only samples of [0, len) are marked
+    const uint32_t prev_w = __shfl_sync(kFull, Mv, (HL - 1) >> 5);
+    const uint32_t next_w = __shfl_sync(kFull, Mv, (HL + TW) >> 5);
+    const int qo = HL >> 5, sh = HL & 31;
+    uint32_t lo_w = __shfl_down_sync(kFull, Mv, qo);
+    uint32_t hi_w = __shfl_down_sync(kFull, Mv, qo + 1 < 32 ? qo + 1 : 31);
+    const uint32_t m_prev = (prev_w >> ((HL - 1) & 31)) & 1u;
+    const uint32_t m_next = (next_w >> ((HL + TW) & 31)) & 1u;
+    if (lane + qo > 31) lo_w = 0u;
+    if (lane + qo + 1 > 31) hi_w = 0u;
+    uint32_t Mt = sh ? ((lo_w >> sh) | (hi_w << (32 - sh))) : lo_w;
+    if (lane >= NWT) Mt = 0u;
+    *edges = m_prev | (m_next << 1);
+    return Mt;
+}
+
+// --------------------------------------------------------------------------- windows + merge (one warp)
+// Marks, island starts and ends, prefix counts and the aggregate of one tile.
+template <int TW>
+__device__ __forceinline__ Agg tile_bits(const KArgs &a, const TileInfo &T, const uint8_t *abyte, TileWords w,
+                                         int16_t *rowtab, int lane)
+{
+    unsigned edges;
+    const uint32_t Mt = tile_marks<TW>(a, T, abyte, &edges, lane);
+    return words_from_marks<TW>(Mt, edges & 1u, edges >> 1, (int)(T.t_end - T.t0), w, rowtab, lane);
 }
 
 // --------------------------------------------------------------------------- cross-tile scan
