@@ -38,7 +38,8 @@ enum daq_status {
     DAQ_ECAPACITY = -2,    /* island records or pool rows did not fit; counts hold the sizes needed */
     DAQ_ECUDA = -3,        /* a CUDA call or kernel launch failed */
     DAQ_ETIMEOUT = -4,     /* a bounded device-side wait gave up; outputs are incomplete */
-    DAQ_EUNSUPPORTED = -5  /* valid request this build does not handle (e.g. n_xtal > 64) */
+    DAQ_EUNSUPPORTED = -5, /* valid request this build does not handle (e.g. n_xtal > 64) */
+    DAQ_ESCRATCH = -6      /* daq_process_fills_static: the call needs more scratch than the built-in area */
 };
 
 /* params->flags */
@@ -223,6 +224,34 @@ typedef struct daq_host_io {
  */
 int daq_process_fills_host(int n_calo, int n_xtal, int64_t n_samples, int n_fills, const daq_params *params,
                            const daq_islands *islands_dev, int64_t *qhist_inout, const daq_host_io *io);
+
+/*
+ * Scratch-free variant (the paper has no counterpart: it concerns how this
+ * library is called, not the method).  For callers that cannot allocate device
+ * memory themselves - code living inside a memory budget fixed at start-up, a
+ * plug-in whose host framework owns every device allocation, or a real-time
+ * loop that must not call an allocator while taking data.  Arguments, outputs
+ * and results are exactly those of daq_process_fills, except that the scratch
+ * workspace comes from an area of DAQ_STATIC_SCRATCH_BYTES built into the
+ * library (params->workspace and params->workspace_bytes are ignored).
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *   - The area exists once per GPU and lives until the process exits; every
+ *     GPU that loads the library holds it.
+ *   - The first call on a device looks up the area's device address (a
+ *     runtime query, made once per device with that device current).  Make
+ *     that first call before any stream capture.
+ *   - Every call uses the same area, and it keeps what the last call left in
+ *     it; each call re-initialises everything it reads.  Calls whose work
+ *     overlaps on the GPU (different streams, or a second call enqueued before
+ *     the first has run) race on the area and give wrong results: serialise
+ *     them.
+ *   - Returns DAQ_ESCRATCH, before touching the GPU, when the call needs more
+ *     than DAQ_STATIC_SCRATCH_BYTES (daq_workspace_size() says how much); one
+ *     full fill of 24 calorimeters x 54 crystals x 560,000 samples fits.
+ */
+#define DAQ_STATIC_SCRATCH_BYTES (8u << 20)
+int daq_process_fills_static(const int16_t *samples, int n_calo, int n_xtal, int64_t n_samples, int n_fills,
+                             const daq_params *params, const daq_islands *islands_out, int64_t *qhist_inout);
 
 /* Upper bound on the tiles of a call with these sizes and parameters (rows of
  * the trace buffer); 0 on invalid arguments. */

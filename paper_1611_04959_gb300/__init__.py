@@ -18,7 +18,8 @@ from . import build as _build
 LIB_PATH = _build.LIB
 
 # status codes and flags (include/daq.h)
-DAQ_OK, DAQ_EINVAL, DAQ_ECAPACITY, DAQ_ECUDA, DAQ_ETIMEOUT, DAQ_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+DAQ_OK, DAQ_EINVAL, DAQ_ECAPACITY, DAQ_ECUDA, DAQ_ETIMEOUT, DAQ_EUNSUPPORTED, DAQ_ESCRATCH = 0, -1, -2, -3, -4, -5, -6
+DAQ_STATIC_SCRATCH_BYTES = 8 << 20
 DAQ_SKIP_Q, DAQ_SKIP_ISLANDS, DAQ_SYNC = 1, 2, 4
 DAQ_DEV_HDR_OVERFLOW, DAQ_DEV_POOL_OVERFLOW, DAQ_DEV_TIMEOUT, DAQ_DEV_BAD_FILL_LEN = 1, 2, 4, 8
 
@@ -75,6 +76,9 @@ def lib():
             L.daq_process_fills.argtypes = [vp, i32, i32, i64, i32, ctypes.POINTER(DaqParams),
                                             ctypes.POINTER(DaqIslands), vp]
             L.daq_process_fills.restype = i32
+            L.daq_process_fills_static.argtypes = [vp, i32, i32, i64, i32, ctypes.POINTER(DaqParams),
+                                                   ctypes.POINTER(DaqIslands), vp]
+            L.daq_process_fills_static.restype = i32
             L.daq_process_fills_host.argtypes = [i32, i32, i64, i32, ctypes.POINTER(DaqParams),
                                                  ctypes.POINTER(DaqIslands), vp, ctypes.POINTER(DaqHostIO)]
             L.daq_process_fills_host.restype = i32
@@ -127,6 +131,13 @@ def daq_process_fills(samples_ptr: int, n_calo: int, n_xtal: int, n_samples: int
                       params: DaqParams, islands: DaqIslands, qhist_ptr: int | None) -> int:
     return int(lib().daq_process_fills(samples_ptr, n_calo, n_xtal, n_samples, n_fills, ctypes.byref(params),
                                        ctypes.byref(islands), qhist_ptr))
+
+
+def daq_process_fills_static(samples_ptr: int, n_calo: int, n_xtal: int, n_samples: int, n_fills: int,
+                             params: DaqParams, islands: DaqIslands, qhist_ptr: int | None) -> int:
+    """daq_process_fills with the library's built-in scratch area (allocates nothing)."""
+    return int(lib().daq_process_fills_static(samples_ptr, n_calo, n_xtal, n_samples, n_fills,
+                                              ctypes.byref(params), ctypes.byref(islands), qhist_ptr))
 
 
 def daq_process_fills_host(n_calo: int, n_xtal: int, n_samples: int, n_fills: int, params: DaqParams,

@@ -1061,6 +1061,7 @@ const char *daq_strerror(int status)
     case DAQ_ECUDA: return "CUDA call or kernel launch failed";
     case DAQ_ETIMEOUT: return "a bounded device-side wait gave up; outputs are incomplete";
     case DAQ_EUNSUPPORTED: return "request not supported by this build";
+    case DAQ_ESCRATCH: return "the call needs more scratch than the library's built-in area holds";
     default: return "unknown status";
     }
 }
