@@ -331,11 +331,6 @@ enum {
     kNBars = kBarMetaFree + kNMeta
 };
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
 // Bounded wait that also returns early once any CTA has flagged a timeout.
 __device__ __forceinline__ bool pipe_wait(const KArgs &a, uint64_t *bar, uint32_t parity)
 {
@@ -668,15 +663,13 @@ static void box_geometry(int width, int X, int *nbox, int *boxw, int *box_stride
 
 static size_t count_smem_bytes(int tw, int slot_bytes, int need_sarr)
 {
-    size_t b = 2 * (size_t)slot_bytes + 128 + (size_t)(tw / 8) * 4 + (need_sarr ? (size_t)tw * 4 : 0);
-    b += 16 + 2 * sizeof(TileInfo) + 2 * 8;
-    return (b + 127) & ~size_t(127);
+    return CountSmem::total(slot_bytes, tw, need_sarr);
 }
 
 static size_t compact_smem_bytes(int tw, int X, int slot_bytes_b)
 {
     size_t b = (size_t)slot_bytes_b + (size_t)(((tw * 2 * X + 32) + 15) & ~15) + (size_t)(tw / 32) * 4 * 6;
-    b += 16 + sizeof(TileInfo) + 2 * sizeof(Agg) + 8;
+    b += 16 + sizeof(TileInfo) + 2 * sizeof(Agg) + 8 + 8 * (kPlanSmem + 1) + 4 * kPlanSmem;
     return (b + 127) & ~size_t(127);
 }
 
@@ -830,7 +823,7 @@ static cudaError_t launch_twopass(const KArgs &a, const Plan &pl, int grid, int 
     int grid_a = grid, grid_b = grid;
     if (grid <= 0) {
         int per_a = 0, per_b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_a, daq_count_kernel<TW>, 256, pl.smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_a, daq_count_kernel<TW>, kCountThreads, pl.smem);
         if (e != cudaSuccess) return e;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_b, daq_compact_kernel<TW>, 256, pl.smem_b);
         if (e != cudaSuccess) return e;
@@ -840,7 +833,7 @@ static cudaError_t launch_twopass(const KArgs &a, const Plan &pl, int grid, int 
     }
     grid_a = (int)std::min<int64_t>(grid_a, tiles);
     grid_b = (int)std::min<int64_t>(grid_b, tiles);
-    daq_count_kernel<TW><<<grid_a, 256, pl.smem, s>>>(a);
+    daq_count_kernel<TW><<<grid_a, kCountThreads, pl.smem, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
     const int scan_blocks = (int)((tiles + kScanChunk - 1) / kScanChunk);

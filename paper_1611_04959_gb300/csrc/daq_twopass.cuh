@@ -43,74 +43,178 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
 // ============================================================================ count pass
+constexpr int kCountSumWarps = 8;
+constexpr int kCountThreads = 32 * (kCountSumWarps + 2);  // + two marks/Q warps, one per buffer
+constexpr int kPlanSmem = 64;                              // fills whose plan is cached in shared memory
+
+// Per-fill plan (first tile, length) in shared memory when the batch has at
+// most kPlanSmem fills; decode_tile then needs one global load (the pedestal).
+struct PlanView {
+    const long long *fts;
+    const int32_t *lens;
+};
+
+__device__ __forceinline__ PlanView cache_plan(const KArgs &a, long long *fts_s, int32_t *lens_s, int tid, int nthr)
+{
+    if (a.n_fills > kPlanSmem) return PlanView{a.fill_tile_start, a.lens};
+    for (int f = tid; f <= a.n_fills; f += nthr) fts_s[f] = a.fill_tile_start[f];
+    for (int f = tid; f < a.n_fills; f += nthr) lens_s[f] = a.lens[f];
+    return PlanView{fts_s, lens_s};
+}
+
+// Bounded mbarrier wait whose outcome is the same in every lane of the warp.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
+{
+    const bool ok = mbar_wait_bounded(bar, parity, kWaitLimitNs);
+    return !__any_sync(kFull, !ok);
+}
+
+// Shared-memory layout of the count kernel, in the order of the buffers.
+struct CountSmem {
+    static size_t __host__ __device__ align16(size_t x) { return (x + 15) & ~size_t(15); }
+    static size_t __host__ __device__ abyte(int slot_bytes) { return 2 * (size_t)slot_bytes; }            // [2][128]
+    static size_t __host__ __device__ blocksum(int slot_bytes) { return abyte(slot_bytes) + 256; }          // [2][TW/8]
+    static size_t __host__ __device__ sarr(int slot_bytes, int tw) { return blocksum(slot_bytes) + (size_t)tw; }  // [2][TW]
+    static size_t __host__ __device__ tinfo(int slot_bytes, int tw, int need_sarr)
+    {
+        return align16(sarr(slot_bytes, tw) + (need_sarr ? 8 * (size_t)tw : 0));  // [4]
+    }
+    static size_t __host__ __device__ fts(int slot_bytes, int tw, int need_sarr)
+    {
+        return tinfo(slot_bytes, tw, need_sarr) + 4 * sizeof(TileInfo);  // [kPlanSmem + 1]
+    }
+    static size_t __host__ __device__ lens(int slot_bytes, int tw, int need_sarr)
+    {
+        return fts(slot_bytes, tw, need_sarr) + 8 * (kPlanSmem + 1);  // [kPlanSmem]
+    }
+    static size_t __host__ __device__ bars(int slot_bytes, int tw, int need_sarr)
+    {
+        return align16(lens(slot_bytes, tw, need_sarr) + 4 * kPlanSmem);  // full[2], sums[2], marks[2]
+    }
+    static size_t __host__ __device__ total(int slot_bytes, int tw, int need_sarr)
+    {
+        return (bars(slot_bytes, tw, need_sarr) + 6 * 8 + 127) & ~size_t(127);
+    }
+};
+
+// Eight sum warps turn a tile into threshold bits and block sums; marks warp
+// s (one per buffer s = j & 1) turns the bits of the CTA's tiles j = s, s + 2,
+// ... into marks words and the tile aggregate and adds the tile's Q bins, while
+// the sum warps go on with the next tile.  Two tile slots are loaded ahead by
+// TMA.  Handoffs (per buffer): full (TMA landed), sums (8 sum warps done: the
+// slot may be refilled and the bits read), marks (bits and block sums read:
+// the buffer may be rewritten).
 template <int TW>
-__global__ void __launch_bounds__(256, 2) daq_count_kernel(const __grid_constant__ KArgs a)
+__global__ void __launch_bounds__(kCountThreads, 2) daq_count_kernel(const __grid_constant__ KArgs a)
 {
     constexpr int NWT = TW / 32, NBT = TW / 8;
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned char *slot0 = smem;
-    uint8_t *abyte = smem + 2 * (size_t)a.slot_bytes;              // 128 bytes
-    int32_t *blocksum = reinterpret_cast<int32_t *>(abyte + 128);  // NBT
-    int32_t *sarr = blocksum + NBT;                                // TW when needed
-    TileInfo *tinfo = reinterpret_cast<TileInfo *>(
-        (reinterpret_cast<uintptr_t>(sarr + (a.need_sarr ? TW : 0)) + 15) & ~uintptr_t(15));  // [2]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(tinfo + 2);                                  // [2]
+    uint8_t *abyte0 = smem + CountSmem::abyte(a.slot_bytes);
+    int32_t *blocksum0 = reinterpret_cast<int32_t *>(smem + CountSmem::blocksum(a.slot_bytes));
+    int32_t *sarr0 = reinterpret_cast<int32_t *>(smem + CountSmem::sarr(a.slot_bytes, TW));
+    TileInfo *tinfo = reinterpret_cast<TileInfo *>(smem + CountSmem::tinfo(a.slot_bytes, TW, a.need_sarr));
+    TileInfo *tinfo_m = tinfo + 2;  // copies handed to the marks warps
+    long long *fts_s = reinterpret_cast<long long *>(smem + CountSmem::fts(a.slot_bytes, TW, a.need_sarr));
+    int32_t *lens_s = reinterpret_cast<int32_t *>(smem + CountSmem::lens(a.slot_bytes, TW, a.need_sarr));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + CountSmem::bars(a.slot_bytes, TW, a.need_sarr));
+    uint64_t *full = bars, *sums = bars + 2, *mdone = bars + 4;
 
-    for (int i = tid; i < 32; i += 256) reinterpret_cast<uint32_t *>(abyte)[i] = 0u;
+    for (int i = tid; i < 64; i += kCountThreads) reinterpret_cast<uint32_t *>(abyte0)[i] = 0u;
+    const PlanView plan = cache_plan(a, fts_s, lens_s, tid, kCountThreads);
     if (tid == 0) {
-        mbar_init(bar, 1);
-        mbar_init(bar + 1, 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(sums + s, kCountSumWarps);
+            mbar_init(mdone + s, 1);
+        }
         fence_mbar_init();
     }
     __syncthreads();
-    const long long total = a.fill_tile_start[a.n_fills];
+    const long long total = plan.fts[a.n_fills];
     const long long G = gridDim.x;
     const int n_steps = (a.ew + 63) / 64;
-    const bool skip_q = (a.flags & DAQ_SKIP_Q) != 0;
+    constexpr int kSumThreads = 32 * kCountSumWarps;
 
     auto start_load = [&](long long tile, int s) {  // thread 0
         TileInfo &T = tinfo[s];
-        decode_tile<TW>(a, tile, T, a.fill_tile_start, a.lens);
+        decode_tile<TW>(a, tile, T, plan.fts, plan.lens);
         trace_stamp(a, tile, 0);
         trace_value(a, tile, 10, sm_id());
         trace_value(a, tile, 11, TW);
-        unsigned char *slot = slot0 + (size_t)s * a.slot_bytes;
         if (a.use_tma) {
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(bar + s, tile_load_bytes(a));
-            issue_tile_load(a, T, slot, bar + s);
+            mbar_arrive_expect_tx(full + s, tile_load_bytes(a));
+            issue_tile_load(a, T, slot0 + (size_t)s * a.slot_bytes, full + s);
         }
         trace_stamp(a, tile, 1);
     };
-    if (tid == 0 && (long long)blockIdx.x < total) start_load(blockIdx.x, 0);
-    for (long long j = 0;; ++j) {
-        const long long tile = blockIdx.x + j * G;
-        if (tile >= total) break;
-        const int s = (int)(j & 1);
-        __syncthreads();  // tinfo[s] is visible; slot s^1 is no longer read
-        if (tid == 0 && tile + G < total) start_load(tile + G, s ^ 1);
-        const TileInfo T = tinfo[s];
-        unsigned char *slot = slot0 + (size_t)s * a.slot_bytes;
-        if (a.use_tma) {
-            const bool ok = mbar_wait_bounded(bar + s, (uint32_t)((j >> 1) & 1), kWaitLimitNs);
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) set_status_bit(a, DAQ_DEV_TIMEOUT);
-                return;
-            }
-        } else {
-            plain_tile_load(a, T, slot, tid, 256);
-            __syncthreads();
+
+    if (warp < kCountSumWarps) {
+        if (tid == 0) {
+            if ((long long)blockIdx.x < total) start_load(blockIdx.x, 0);
+            if ((long long)blockIdx.x + G < total) start_load(blockIdx.x + G, 1);
         }
-        if (tid == 0) trace_stamp(a, T.tile, 2);
-        const uint32_t slot_s = smem_addr(slot);
-        for (int it = warp; it < n_steps; it += 8)
-            sum_pass_step(a, T, slot_s, it, NBT, abyte, blocksum, sarr, nullptr, lane);
-        __syncthreads();
-        if (tid == 0) trace_stamp(a, T.tile, 3);
-        if (warp == 0) {
+        for (long long j = 0;; ++j) {
+            const long long tile = blockIdx.x + j * G;
+            if (tile >= total) break;
+            const int s = (int)(j & 1);
+            const uint32_t par = (uint32_t)((j >> 1) & 1);
+            unsigned char *slot = slot0 + (size_t)s * a.slot_bytes;
+            if (a.use_tma) {
+                if (!warp_wait(full + s, par)) {
+                    if (lane == 0) set_status_bit(a, DAQ_DEV_TIMEOUT);
+                    break;
+                }
+            } else {
+                // sum warps only: the slot's previous tile (j - 2) is done and tinfo[s] is decoded
+                asm volatile("bar.sync 1, %0;" ::"r"(kSumThreads) : "memory");
+                plain_tile_load(a, tinfo[s], slot, tid, kSumThreads);
+                asm volatile("bar.sync 1, %0;" ::"r"(kSumThreads) : "memory");
+            }
+            if (j >= 2 && !warp_wait(mdone + s, par ^ 1u)) {
+                if (lane == 0) set_status_bit(a, DAQ_DEV_TIMEOUT);
+                break;
+            }
+            const TileInfo T = tinfo[s];
+            if (tid == 0) {
+                trace_stamp(a, T.tile, 2);
+                tinfo_m[s] = T;
+            }
+            const uint32_t slot_s = smem_addr(slot);
+            for (int it = warp; it < n_steps; it += kCountSumWarps)
+                sum_pass_step(a, T, slot_s, it, NBT, abyte0 + 128 * s, blocksum0 + NBT * s,
+                              sarr0 + (a.need_sarr ? TW * s : 0), nullptr, lane);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(sums + s);
+            if (tid == 0) {
+                trace_stamp(a, T.tile, 3);
+                // slot s takes tile j + 2 once every sum warp is done with tile j
+                if (tile + 2 * G < total) {
+                    if (mbar_wait_bounded(sums + s, par, kWaitLimitNs)) {
+                        if (a.use_tma) start_load(tile + 2 * G, s);
+                        else decode_tile<TW>(a, tile + 2 * G, tinfo[s], plan.fts, plan.lens);
+                    } else {
+                        set_status_bit(a, DAQ_DEV_TIMEOUT);  // the other warps time out on tile j + 2
+                    }
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ marks, aggregate, Q bins of buffer s
+        const int s = warp - kCountSumWarps;
+        const bool skip_q = (a.flags & DAQ_SKIP_Q) != 0;
+        for (long long j = s;; j += 2) {
+            const long long tile = blockIdx.x + j * G;
+            if (tile >= total) break;
+            if (!warp_wait(sums + s, (uint32_t)((j >> 1) & 1))) {
+                if (lane == 0) set_status_bit(a, DAQ_DEV_TIMEOUT);
+                break;
+            }
+            const TileInfo T = tinfo_m[s];
             unsigned edges;
-            const uint32_t Mt = tile_marks<TW>(a, T, abyte, &edges, lane);
+            const uint32_t Mt = tile_marks<TW>(a, T, abyte0 + 128 * s, &edges, lane);
             const Agg agg = words_from_marks<TW>(Mt, edges & 1u, edges >> 1, (int)(T.t_end - T.t0),
                                                  TileWords{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
                                                  nullptr, lane);
@@ -124,8 +228,9 @@ __global__ void __launch_bounds__(256, 2) daq_count_kernel(const __grid_constant
                 reinterpret_cast<TileRec *>(a.recs)[T.tile] = r;
                 trace_stamp(a, T.tile, 4);
             }
-        } else if (!skip_q) {
-            q_partial(a, T, blocksum, sarr, tid - 32, 256 - 32);
+            if (!skip_q) q_partial(a, T, blocksum0 + NBT * s, sarr0 + (a.need_sarr ? TW * s : 0), lane, 32);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(mdone + s);
         }
     }
 }
@@ -285,6 +390,10 @@ __device__ __forceinline__ void plain_tile_load_b(const KArgs &a, const TileInfo
     }
 }
 
+// One tile slot: the next tile's load is issued as soon as the current tile's
+// rows are staged, so it lands while the pool rows and island records of the
+// current tile are written; the marks, record and prefix of the next tile are
+// loaded into registers at the same point.
 template <int TW>
 __global__ void __launch_bounds__(256, 2) daq_compact_kernel(const __grid_constant__ KArgs a)
 {
@@ -302,56 +411,72 @@ __global__ void __launch_bounds__(256, 2) daq_compact_kernel(const __grid_consta
     Agg *s_ex = reinterpret_cast<Agg *>(tinfo + 1);
     Agg *s_agg = s_ex + 1;
     uint64_t *bar = reinterpret_cast<uint64_t *>(s_agg + 1);
+    long long *fts_s = reinterpret_cast<long long *>(bar + 1);        // [kPlanSmem + 1]
+    int32_t *lens_s = reinterpret_cast<int32_t *>(fts_s + kPlanSmem + 1);  // [kPlanSmem]
+    const PlanView plan = cache_plan(a, fts_s, lens_s, tid, 256);
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
-    const long long total = a.fill_tile_start[a.n_fills];
+    const long long total = plan.fts[a.n_fills];
     const TileRec *recs = reinterpret_cast<const TileRec *>(a.recs);
     const TileExcl *exs = reinterpret_cast<const TileExcl *>(a.excl);
+    const uint32_t box_bytes = (uint32_t)a.nbox_b * (uint32_t)X * (uint32_t)a.rs_b;
+
+    auto start_load = [&](long long tile) {  // one thread
+        decode_tile<TW>(a, tile, *tinfo, plan.fts, plan.lens);
+        trace_stamp(a, tile, 5);
+        if (a.use_tma) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, box_bytes);
+            issue_tile_load_b(a, *tinfo, slot, bar);
+        }
+    };
+    // warp 0's inputs of the next tile, in registers
+    auto load_inputs = [&](long long tile, uint32_t &Mt, TileRec &r, TileExcl &e) {
+        Mt = lane < NWT ? a.marks[tile * NWT + lane] : 0u;
+        r = recs[tile];
+        e = exs[tile];
+    };
+
     uint32_t phase_bit = 0;
     bool store_pending = false;
+    uint32_t nMt = 0;
+    TileRec nr{0, 0, 0, 0};
+    TileExcl ne{0, 0, 0};
+    if ((long long)blockIdx.x < total) {
+        if (tid == 32) start_load(blockIdx.x);
+        if (warp == 0) load_inputs(blockIdx.x, nMt, nr, ne);
+    }
     for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        if (tid == 0) {
-            decode_tile<TW>(a, tile, *tinfo, a.fill_tile_start, a.lens);
-            trace_stamp(a, tile, 5);
-            if (a.use_tma) {
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(bar, (uint32_t)a.nbox_b * (uint32_t)X * (uint32_t)a.rs_b);
-                issue_tile_load_b(a, *tinfo, slot, bar);
-            }
-        }
-        __syncthreads();
+        __syncthreads();  // tinfo holds this tile
         const TileInfo T = *tinfo;
         if (!a.use_tma) plain_tile_load_b(a, T, slot, tid, 256);
         if (warp == 0) {
-            const TileRec r = recs[tile];
-            const TileExcl e = exs[tile];
-            const uint32_t Mt = lane < NWT ? a.marks[tile * NWT + lane] : 0u;
-            const Agg g = words_from_marks<TW>(Mt, (r.flags >> 1) & 1, (r.flags >> 2) & 1, (int)(T.t_end - T.t0),
-                                               W, nullptr, lane);
+            const Agg g = words_from_marks<TW>(nMt, (nr.flags >> 1) & 1, (nr.flags >> 2) & 1,
+                                               (int)(T.t_end - T.t0), W, nullptr, lane);
             if (lane == 0) {
                 Agg ex;
-                ex.m = e.m;
-                ex.s = e.s;
-                ex.tr = e.tr;
+                ex.m = ne.m;
+                ex.s = ne.s;
+                ex.tr = ne.tr;
                 ex.full = 0;
                 ex.poison = 0;
                 *s_ex = ex;
                 *s_agg = g;
+                if (store_pending) {  // the stage is free once the last bulk store has read it
+                    bulk_wait_read0();
+                    store_pending = false;
+                }
             }
-        }
-        if (tid == 0 && store_pending) {  // the stage is free once the last bulk store has read it
-            bulk_wait_read0();
-            store_pending = false;
         }
         if (a.use_tma) {
             const bool ok = mbar_wait_bounded(bar, phase_bit, kWaitLimitNs);
             phase_bit ^= 1u;
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) set_status_bit(a, DAQ_DEV_TIMEOUT);
-                return;
+                break;
             }
         } else {
             __syncthreads();
@@ -364,7 +489,12 @@ __global__ void __launch_bounds__(256, 2) daq_compact_kernel(const __grid_consta
         const int nt = (int)(T.t_end - T.t0);
         for (int it = warp; it < (nt + 63) / 64; it += 8) compact_step(a, smem_addr(slot), it, nt, W.m, W.mb, stage,
                                                                         phase, lane);
-        __syncthreads();
+        __syncthreads();  // rows staged; the slot is free
+        const long long next = tile + gridDim.x;
+        if (next < total) {
+            if (tid == 32) start_load(next);
+            if (warp == 0) load_inputs(next, nMt, nr, ne);
+        }
         if (tid == 0) trace_stamp(a, tile, 7);
         // rows [ex.m, ex.m + agg.m) <- stage bytes [phase, phase + agg.m * 2X)
         long long ge = gs + agg.m * rb;
@@ -386,11 +516,11 @@ __global__ void __launch_bounds__(256, 2) daq_compact_kernel(const __grid_consta
                 store_pending = true;
             }
             const int n_head = (int)((a16 - gs) >> 1), n_tail = (int)((ge - b16) >> 1);
-            if (tid >= 32 && tid < 32 + n_head)
-                *reinterpret_cast<uint16_t *>(g + gs + 2 * (tid - 32)) =
-                    *reinterpret_cast<const uint16_t *>(stage + phase + 2 * (tid - 32));
-            else if (tid >= 64 && tid < 64 + n_tail) {
-                const long long o = b16 + 2 * (tid - 64);
+            if (tid >= 64 && tid < 64 + n_head)
+                *reinterpret_cast<uint16_t *>(g + gs + 2 * (tid - 64)) =
+                    *reinterpret_cast<const uint16_t *>(stage + phase + 2 * (tid - 64));
+            else if (tid >= 96 && tid < 96 + n_tail) {
+                const long long o = b16 + 2 * (tid - 96);
                 *reinterpret_cast<uint16_t *>(g + o) = *reinterpret_cast<const uint16_t *>(stage + phase + (o - gs));
             }
         }
