@@ -305,6 +305,10 @@ def bench_gb300(args, ws, rank, local):
         "clocks": clocks.summary(),
     }
 
+    # ---- batched form: 16 uneven fills in one tuned, graph-captured launch
+    if not args.no_batched and not args.quick:
+        result["batched"] = bench_batched(args, torch, dev, daq, synth, W)
+
     # ---- plain form: one CTA per tile, no persistence
     if not args.quick:
         pp, _ = make_p(grid=-1)
@@ -367,6 +371,70 @@ def bench_gb300(args, ws, rank, local):
     return result if rank == 0 else None
 
 
+def bench_batched(args, torch, dev, daq, synth, W) -> dict:
+    """The batching workload: 16 fills x 24 calorimeters, lengths uniform in
+    [80k, 560k] samples and pulse rates x log-uniform[0.2, 5], processed by
+    one tuned plan replayed as a CUDA graph; Q accumulates over the fills."""
+    import numpy as np
+    w = W.BATCH_UNEVEN
+    params = w.params()
+    fl, rate = w.plan()
+    F, C, X, N = w.n_fills, w.n_calo, 54, w.n_samples
+    cfg = w.config()
+    samples = torch.empty((F, C, X, N), dtype=torch.int16, device=dev)
+    stage = torch.empty((1, C, X, N), dtype=torch.int16).pin_memory()
+    t0 = time.perf_counter()
+    for f in range(F):
+        synth.generate(cfg, fill_len=fl, rate=rate, out=stage.numpy(), n_threads=os.cpu_count() or 1,
+                       fills=(f, 1))
+        samples[f].copy_(stage[0], non_blocking=False)
+    gen_s = time.perf_counter() - t0
+    del stage
+    raw = int(C * X * 2 * int(np.asarray(fl, np.int64).sum()))
+    rows = C * int(np.asarray(fl, np.int64).sum())
+    out = daq.Outputs(torch, dev, F, C, X, rows // 4 + F * C + 1, rows)
+    q = torch.zeros(daq.q_size(C, N, params["decim"]), dtype=torch.int64, device=dev)
+    fl_d = torch.as_tensor(np.asarray(fl, np.int32), device=dev)
+    t1 = time.perf_counter()
+    plan = daq.BatchPlan(samples, q, out, fill_len=fl_d, tune=True, **params)
+    tune_s = time.perf_counter() - t1
+    tuning = plan.tuning()
+    stream = torch.cuda.Stream(dev)
+    for _ in range(3):
+        plan.launch(stream)
+    torch.cuda.synchronize(dev)
+    counts = out.counts.cpu().numpy()
+    status = daq.daq_status_from_counts(counts)
+    if status != daq.DAQ_OK:
+        raise daq.DaqError(status, "batched warm-up")
+    Kb = max(3, min(args.steps, args.batched_steps))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(Kb)]
+    for k in range(Kb):
+        evs[k][0].record(stream)
+        plan.launch(stream)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = evs[0][0].elapsed_time(evs[-1][1])
+    plan.close()
+    res = {"value": round(Kb * raw / (total_ms * 1e-3) / 1e9, 2), "unit": UNIT, "steps": Kb,
+           "ms_per_batch": round(total_ms / Kb, 4),
+           "latency_ms": {"p50": round(statistics.median(ms), 4), "p99": round(float(np.percentile(ms, 99)), 4)},
+           "pct_of_hbm_peak": round(100.0 * Kb * raw / (total_ms * 1e-3) / 1e9 / measured_peaks()[0], 2),
+           "workload": "16 fills x 24 calorimeters x 54 crystals, lengths uniform in [80k, 560k] samples "
+                       "(pitch 560,000), pulse rate x log-uniform[0.2, 5] per fill, T=30, pre=8, post=24, D=32",
+           "raw_bytes_per_batch": raw, "islands_per_batch": int(counts[0]), "pool_rows_per_batch": int(counts[1]),
+           "coverage": round(int(counts[1]) / rows, 4),
+           "launch": "one CUDA graph launch per batch (daq_batch_plan_create / daq_batch_launch)",
+           "tuned": {"tile": tuning["tile"], "grid": tuning["grid"], "candidates": tuning["n_tried"],
+                     "ms": round(tuning["ms"], 4), "ms_default_config": round(tuning["ms_default"], 4),
+                     "tuning_s": round(tune_s, 2)},
+           "gpu_launches": 5 * Kb, "generation_s": round(gen_s, 1)}
+    del samples, out, q
+    torch.cuda.empty_cache()
+    return res
+
+
 # ----------------------------------------------------------------------------- reference arm (oracle)
 def bench_reference(args, ws, rank, local):
     if rank != 0:
@@ -423,7 +491,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--quick", action="store_true", help="skip the plain-form comparison")
+    ap.add_argument("--quick", action="store_true", help="main measurement only (no plain or batched form)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 16-fill batched form")
+    ap.add_argument("--batched-steps", type=int, default=30)
     ap.add_argument("--calos", type=int, default=24, help="calorimeters per fill (24; fewer only for profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

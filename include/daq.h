@@ -253,6 +253,63 @@ int daq_process_fills_host(int n_calo, int n_xtal, int64_t n_samples, int n_fill
 int daq_process_fills_static(const int16_t *samples, int n_calo, int n_xtal, int64_t n_samples, int n_fills,
                              const daq_params *params, const daq_islands *islands_out, int64_t *qhist_inout);
 
+/*
+ * Batch plans (the batching pattern: many calorimeter-fills of uneven length
+ * and pulse rate in one launch).  A plan binds one batch - the same pointers,
+ * sizes and parameters as daq_process_fills - to a tuned configuration and a
+ * CUDA graph of the whole launch sequence, so that each daq_batch_launch is a
+ * single graph launch with no host-side planning.
+ *
+ * daq_batch_plan_create
+ *   samples ... qhist_inout  exactly as for daq_process_fills.  The graph reads
+ *                the samples and params->fill_len (values may change between
+ *                launches, pointers may not) and writes islands_out at every
+ *                launch; qhist_inout receives each launch's bins.
+ *   params       as for daq_process_fills; params->stream is not used (each
+ *                launch names its stream).  params->workspace may be NULL: the
+ *                plan then allocates and owns one.  With DAQ_TUNE, params->tile
+ *                and params->grid are ignored and chosen by the tuner.
+ *   plan_flags   DAQ_TUNE: time the candidate configurations (two-pass form at
+ *                tile widths 128/224/448 with 2 or 1 CTAs per SM; the
+ *                single-pass forms) on this batch and keep the fastest.  The
+ *                choice is remembered per (device, sizes, windows, decimation,
+ *                flags) for the rest of the process.  DAQ_TUNE_FORCE: ignore a
+ *                remembered choice.
+ *   *plan        receives the plan (NULL on error).
+ * Creation is not the hot call: it may allocate, synchronises the device, and
+ * runs the batch several times (tuning and a warm-up run) with islands_out as
+ * output and a scratch Q histogram, so qhist_inout is untouched until the first
+ * daq_batch_launch.  Returns DAQ_EINVAL for invalid arguments (checked before
+ * any GPU work), else the status of the warm-up run or DAQ_ECUDA.
+ *
+ * daq_batch_launch       enqueue one replay on `stream` (cudaStream_t).  Replays
+ *                        share the plan's workspace and outputs: serialise them.
+ * daq_batch_plan_tuning  the chosen configuration and the timings behind it.
+ * daq_batch_plan_destroy free the graph, stream and plan-owned workspace.
+ * daq_tune_cache_clear   forget every remembered tuning choice.
+ */
+#define DAQ_TUNE 1u
+#define DAQ_TUNE_FORCE 2u
+
+typedef struct daq_batch_plan daq_batch_plan;
+
+typedef struct daq_tune_result {
+    int32_t tile;      /* chosen daq_params.tile */
+    int32_t grid;      /* chosen daq_params.grid */
+    int32_t n_tried;   /* candidates timed (0 if not tuned or taken from the cache) */
+    int32_t from_cache;
+    float ms;          /* mean time per run of the chosen candidate (ms), 0 if not timed */
+    float ms_default;  /* the same for the default configuration (tile 448, grid 0) */
+} daq_tune_result;
+
+int daq_batch_plan_create(const int16_t *samples, int n_calo, int n_xtal, int64_t n_samples, int n_fills,
+                          const daq_params *params, const daq_islands *islands_out, int64_t *qhist_inout,
+                          uint32_t plan_flags, daq_batch_plan **plan);
+int daq_batch_launch(daq_batch_plan *plan, void *stream);
+int daq_batch_plan_tuning(const daq_batch_plan *plan, daq_tune_result *out);
+int daq_batch_plan_destroy(daq_batch_plan *plan);
+void daq_tune_cache_clear(void);
+
 /* Upper bound on the tiles of a call with these sizes and parameters (rows of
  * the trace buffer); 0 on invalid arguments. */
 int64_t daq_trace_tiles(int n_calo, int n_xtal, int64_t n_samples, int n_fills, const daq_params *params);

@@ -47,6 +47,14 @@ class DaqHostIO(ctypes.Structure):
                 ("pedestal_host", ctypes.c_void_p), ("counts_host", ctypes.c_void_p)]
 
 
+class DaqTuneResult(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("grid", ctypes.c_int32), ("n_tried", ctypes.c_int32),
+                ("from_cache", ctypes.c_int32), ("ms", ctypes.c_float), ("ms_default", ctypes.c_float)]
+
+
+DAQ_TUNE, DAQ_TUNE_FORCE = 1, 2
+
+
 class DaqError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -90,6 +98,18 @@ def lib():
             L.daq_strerror.restype = ctypes.c_char_p
             L.daq_version.argtypes = []
             L.daq_version.restype = i32
+            L.daq_batch_plan_create.argtypes = [vp, i32, i32, i64, i32, ctypes.POINTER(DaqParams),
+                                                ctypes.POINTER(DaqIslands), vp, ctypes.c_uint32,
+                                                ctypes.POINTER(vp)]
+            L.daq_batch_plan_create.restype = i32
+            L.daq_batch_launch.argtypes = [vp, vp]
+            L.daq_batch_launch.restype = i32
+            L.daq_batch_plan_tuning.argtypes = [vp, ctypes.POINTER(DaqTuneResult)]
+            L.daq_batch_plan_tuning.restype = i32
+            L.daq_batch_plan_destroy.argtypes = [vp]
+            L.daq_batch_plan_destroy.restype = i32
+            L.daq_tune_cache_clear.argtypes = []
+            L.daq_tune_cache_clear.restype = None
             _lib = L
     return _lib
 
@@ -144,6 +164,35 @@ def daq_process_fills_host(n_calo: int, n_xtal: int, n_samples: int, n_fills: in
                            islands_dev: DaqIslands, qhist_ptr: int | None, io: DaqHostIO) -> int:
     return int(lib().daq_process_fills_host(n_calo, n_xtal, n_samples, n_fills, ctypes.byref(params),
                                             ctypes.byref(islands_dev), qhist_ptr, ctypes.byref(io)))
+
+
+def daq_batch_plan_create(samples_ptr: int, n_calo: int, n_xtal: int, n_samples: int, n_fills: int,
+                          params: DaqParams, islands: DaqIslands, qhist_ptr: int | None, plan_flags: int):
+    """Returns (status, plan handle or None)."""
+    h = ctypes.c_void_p()
+    rc = lib().daq_batch_plan_create(samples_ptr, n_calo, n_xtal, n_samples, n_fills, ctypes.byref(params),
+                                     ctypes.byref(islands), qhist_ptr, int(plan_flags), ctypes.byref(h))
+    return int(rc), h.value
+
+
+def daq_batch_launch(plan, stream_ptr: int | None) -> int:
+    return int(lib().daq_batch_launch(plan, stream_ptr))
+
+
+def daq_batch_plan_tuning(plan) -> DaqTuneResult:
+    r = DaqTuneResult()
+    rc = lib().daq_batch_plan_tuning(plan, ctypes.byref(r))
+    if rc:
+        raise DaqError(rc, "daq_batch_plan_tuning")
+    return r
+
+
+def daq_batch_plan_destroy(plan) -> int:
+    return int(lib().daq_batch_plan_destroy(plan))
+
+
+def daq_tune_cache_clear() -> None:
+    lib().daq_tune_cache_clear()
 
 
 def daq_status_from_counts(counts_host) -> int:
@@ -236,3 +285,49 @@ def process_fills(samples, threshold=30, pre=8, post=24, ped_samples=100, decim=
         counts = outputs.counts.cpu().numpy()
         res.update(counts=counts, n_islands=int(counts[0]), n_rows=int(counts[1]))
     return res
+
+
+class BatchPlan:
+    """A tuned, graph-captured batch (daq_batch_plan_create / daq_batch_launch).
+
+    Keeps references to every tensor the graph reads or writes."""
+
+    def __init__(self, samples, q, outputs: Outputs, threshold=30, pre=8, post=24, ped_samples=100, decim=(32,),
+                 fill_len=None, fill_base=0, flags=0, tile=0, grid=0, tune=True, force=False, workspace=None):
+        import torch
+        if not samples.is_cuda or samples.dtype != torch.int16 or samples.dim() != 4 or not samples.is_contiguous():
+            raise ValueError("samples must be a contiguous CUDA int16 tensor [fills][calo][xtal][samples]")
+        F, C, X, N = (int(v) for v in samples.shape)
+        self.shape = (F, C, X, N)
+        self._keep = (samples, q, outputs, fill_len, workspace)
+        self.outputs = outputs
+        self.q = q
+        p = make_params(threshold, pre, post, ped_samples, decim, fill_base, fill_len, flags, tile, grid, None,
+                        workspace)
+        pf = (DAQ_TUNE if tune else 0) | (DAQ_TUNE_FORCE if force else 0)
+        rc, h = daq_batch_plan_create(samples.data_ptr(), C, X, N, F, p, outputs.struct(),
+                                      None if q is None else q.data_ptr(), pf)
+        if rc != DAQ_OK:
+            raise DaqError(rc, "daq_batch_plan_create")
+        self._h = h
+
+    def launch(self, stream=None) -> None:
+        rc = daq_batch_launch(self._h, None if stream is None else int(stream.cuda_stream))
+        if rc != DAQ_OK:
+            raise DaqError(rc, "daq_batch_launch")
+
+    def tuning(self) -> dict:
+        r = daq_batch_plan_tuning(self._h)
+        return dict(tile=r.tile, grid=r.grid, n_tried=r.n_tried, from_cache=bool(r.from_cache), ms=r.ms,
+                    ms_default=r.ms_default)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            daq_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

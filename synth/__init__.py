@@ -66,6 +66,9 @@ def _load():
             lib.synth_generate.argtypes = [P(SynthConfig), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int]
             lib.synth_generate.restype = ctypes.c_int
+            lib.synth_generate_fills.argtypes = [P(SynthConfig), ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+            lib.synth_generate_fills.restype = ctypes.c_int
             lib.synth_fill_plan.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
                                             ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
             lib.synth_fill_plan.restype = ctypes.c_int
@@ -95,22 +98,25 @@ def make_config(**kw) -> SynthConfig:
     return SynthConfig(**d)
 
 
-def generate(cfg: SynthConfig, fill_len=None, rate=None, out=None, n_threads: int = 0) -> np.ndarray:
+def generate(cfg: SynthConfig, fill_len=None, rate=None, out=None, n_threads: int = 0, fills=None) -> np.ndarray:
     """Return (or fill) samples[n_fills][n_calo][n_rows*n_cols][n_samples] int16.
 
-    `out` may be any C-contiguous int16 buffer of that size (e.g. a pinned
-    host tensor's numpy view)."""
+    `fills` = (f0, n) generates only fills f0 .. f0 + n - 1 (their bytes equal
+    those of a whole-batch call; fill_len / rate stay indexed by the absolute
+    fill).  `out` may be any C-contiguous int16 buffer of that size (e.g. a
+    pinned host tensor's numpy view)."""
     lib = _load()
-    shape = (cfg.n_fills, cfg.n_calo, cfg.n_rows * cfg.n_cols, cfg.n_samples)
+    f0, nf = (0, cfg.n_fills) if fills is None else (int(fills[0]), int(fills[1]))
+    shape = (nf, cfg.n_calo, cfg.n_rows * cfg.n_cols, cfg.n_samples)
     if out is None:
         out = np.empty(shape, dtype=np.int16)
     assert out.dtype == np.int16 and out.flags.c_contiguous and out.size == int(np.prod(shape))
     fl = None if fill_len is None else np.ascontiguousarray(fill_len, dtype=np.int32)
     rt = None if rate is None else np.ascontiguousarray(rate, dtype=np.float64)
-    rc = lib.synth_generate(ctypes.byref(cfg), None if fl is None else fl.ctypes.data,
-                            None if rt is None else rt.ctypes.data, out.ctypes.data, int(n_threads))
+    rc = lib.synth_generate_fills(ctypes.byref(cfg), f0, nf, None if fl is None else fl.ctypes.data,
+                                  None if rt is None else rt.ctypes.data, out.ctypes.data, int(n_threads))
     if rc != 0:
-        raise ValueError("synth_generate rejected the configuration")
+        raise ValueError("synth_generate_fills rejected the configuration")
     return out
 
 

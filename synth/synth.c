@@ -331,19 +331,21 @@ int synth_fill_plan(uint64_t seed, int32_t n_fills, int64_t len_lo, int64_t len_
     return 0;
 }
 
-/* Fill out[F][C][X][n_samples].  fill_len / rate may be NULL (all n_samples / 1.0). */
-int synth_generate(const synth_config *cfg, const int32_t *fill_len, const double *rate, int16_t *out,
-                   int n_threads)
+/* Fill out[n][C][X][n_samples] with fills [f0, f0 + n) of the configuration
+ * (bytes identical to those fills in a whole-batch call).  fill_len / rate are
+ * indexed by the absolute fill and may be NULL (all n_samples / 1.0). */
+int synth_generate_fills(const synth_config *cfg, int32_t f0, int32_t n, const int32_t *fill_len,
+                         const double *rate, int16_t *out, int n_threads)
 {
     if (!cfg || !out || cfg->n_fills < 0 || cfg->n_calo < 0 || cfg->n_rows <= 0 || cfg->n_cols <= 0 ||
-        cfg->n_samples < 0 || cfg->ped_hi < cfg->ped_lo)
+        cfg->n_samples < 0 || cfg->ped_hi < cfg->ped_lo || f0 < 0 || n < 0 || f0 + n > cfg->n_fills)
         return -1;
     const int64_t n_x = (int64_t)cfg->n_rows * cfg->n_cols, pitch = cfg->n_samples;
     int64_t cum_len = pitch > (int64_t)cfg->nominal_samples ? pitch : (int64_t)cfg->nominal_samples;
     double *cum = intensity_cumulative(cfg, cum_len);
     noise_table nt;
     noise_table_init(&nt, cfg->noise_sigma);
-    const int64_t n_cf = (int64_t)cfg->n_fills * cfg->n_calo;
+    const int64_t n_cf = (int64_t)n * cfg->n_calo;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel
@@ -354,9 +356,10 @@ int synth_generate(const synth_config *cfg, const int32_t *fill_len, const doubl
 #pragma omp for schedule(dynamic, 1)
 #endif
         for (int64_t cf = 0; cf < n_cf; ++cf) {
-            int f = (int)(cf / cfg->n_calo), c = (int)(cf % cfg->n_calo);
+            int f = f0 + (int)(cf / cfg->n_calo), c = (int)(cf % cfg->n_calo);
             int64_t len = fill_len ? fill_len[f] : pitch;
             if (len < 0) len = 0;
+            if (len > pitch) len = pitch;
             double rt = rate ? rate[f] : 1.0;
             render_calofill(cfg, &nt, cum, cum_len, f, c, len, rt, out + cf * n_x * pitch, sig);
         }
@@ -365,6 +368,14 @@ int synth_generate(const synth_config *cfg, const int32_t *fill_len, const doubl
     free(nt.thr);
     free(cum);
     return 0;
+}
+
+/* Fill out[F][C][X][n_samples].  fill_len / rate may be NULL (all n_samples / 1.0). */
+int synth_generate(const synth_config *cfg, const int32_t *fill_len, const double *rate, int16_t *out,
+                   int n_threads)
+{
+    if (!cfg) return -1;
+    return synth_generate_fills(cfg, 0, cfg->n_fills, fill_len, rate, out, n_threads);
 }
 
 /* Truth list of one calorimeter-fill, in arrival order.  Returns the pulse
