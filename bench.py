@@ -309,6 +309,10 @@ def bench_gb300(args, ws, rank, local):
     if not args.no_batched and not args.quick:
         result["batched"] = bench_batched(args, torch, dev, daq, synth, W)
 
+    # ---- served form: request loop with admission, overlap and resident Q
+    if not args.no_served and not args.quick:
+        result["served"] = bench_served(args, torch, dev, daq, synth, W, samples)
+
     # ---- plain form: one CTA per tile, no persistence
     if not args.quick:
         pp, _ = make_p(grid=-1)
@@ -435,6 +439,89 @@ def bench_batched(args, torch, dev, daq, synth, W) -> dict:
     return res
 
 
+def burst_schedule(n_fills: int, speed: float, t0_us: float) -> list:
+    """Arrival times (us) of the accelerator cycle replayed `speed` times
+    faster: bursts of 8 fills 10 ms apart, two bursts per 1.4 s cycle (the
+    second half a cycle after the first)."""
+    cycle, spacing = 1.4e6 / speed, 10e3 / speed
+    out = []
+    for i in range(n_fills):
+        c, b, k = i // 16, (i // 8) % 2, i % 8
+        out.append(t0_us + c * cycle + b * cycle / 2 + k * spacing)
+    return out
+
+
+def bench_served(args, torch, dev, daq, synth, W, samples0) -> dict:
+    """The serving workload: a stream of 24-calorimeter fills arriving in the
+    accelerator's burst pattern at 1x, 10x and 100x, served by the request
+    loop (40 GB slot budget, 4 streams, Q resident across every fill) from a
+    pool of device-resident fills; plus a saturated run (all fills at once)."""
+    import numpy as np
+    w = W.SERVING
+    params = w.params()
+    C, X, N = w.n_calo, 54, w.n_samples
+    n_pool = max(1, args.serve_pool)
+    cfg = W.scaled(w, n_fills=n_pool).config()
+    pool = [samples0[0]]
+    stage = torch.empty((1, C, X, N), dtype=torch.int16).pin_memory()
+    for f in range(1, n_pool):
+        synth.generate(cfg, out=stage.numpy(), n_threads=os.cpu_count() or 1, fills=(f, 1))
+        pool.append(stage[0].to(dev))
+    del stage
+    budget = 40 << 30
+    srv = daq.DaqServer(C, X, N, budget, **params, n_streams=4, auto_release=True, device=dev)
+    st0 = srv.stats()
+    # warm-up
+    for k in range(4):
+        srv.submit(pool[k % n_pool])
+    srv.drain(120.0)
+    srv.records(clear=True)
+    rates = {}
+    for speed, n in ((1, args.serve_fills_1x), (10, args.serve_fills), (100, args.serve_fills)):
+        t0 = srv.now_us() + 50e3
+        arr = burst_schedule(n, speed, t0)
+        with ClockSampler(dev.index or 0) as clk:
+            for i, a in enumerate(arr):
+                srv.submit(pool[i % n_pool], arrival_us=a)
+            srv.drain(600.0)
+        recs = srv.records(clear=True)
+        sm = daq.daq_serving_summarize(recs)
+        lat = [r.t_done - r.t_arrival for r in recs]
+        offered = n * C * X * N * 2 / ((arr[-1] - arr[0]) * 1e-6) / 1e9 if n > 1 else None
+        rates[f"{speed}x"] = {"fills": n, "fill_spacing_ms": 10.0 / speed, "cycle_ms": 1400.0 / speed,
+                              "latency_ms": {"p50": round(sm.latency_p50_us / 1e3, 4),
+                                             "p99": round(sm.latency_p99_us / 1e3, 4),
+                                             "max": round(sm.latency_max_us / 1e3, 4)},
+                              "p99_under_fill_spacing": bool(sm.latency_p99_us < 10e3 / speed),
+                              "deadtime": round(sm.deadtime, 4),
+                              "served_gbs": round(sm.gbs, 2),
+                              "offered_gbs": None if offered is None else round(offered, 2),
+                              "clocks": clk.summary()}
+        assert all(r.status == 0 for r in recs), "served fill failed"
+        del lat
+    # saturated: every fill arrives at once; throughput of the overlapped stream
+    n_sat = args.serve_fills_saturated
+    for i in range(n_sat):
+        srv.submit(pool[i % n_pool])
+    srv.drain(600.0)
+    recs = srv.records(clear=True)
+    sm = daq.daq_serving_summarize(recs)
+    busy = max(r.t_done for r in recs) - min(r.t_start for r in recs)
+    sat_gbs = n_sat * C * X * N * 2 / (busy * 1e-6) / 1e9
+    st = srv.stats()
+    srv.close()
+    return {"workload": "stream of 24 x 54 x 560,000 int16 fills (1.4515 GB each) from a pool of "
+                        f"{n_pool} device-resident generated fills; bursts of 8 fills 10 ms apart, 2 bursts per "
+                        "1.4 s cycle, replayed at 1x / 10x / 100x; T=30, pre=8, post=24, D=32",
+            "budget_bytes": budget, "slots": st0["n_slots"], "slot_bytes": st0["slot_bytes"],
+            "streams": st0["n_streams"], "rates": rates,
+            "saturated": {"value": round(sat_gbs, 2), "unit": UNIT, "fills": n_sat,
+                          "pct_of_hbm_peak": round(100.0 * sat_gbs / measured_peaks()[0], 2),
+                          "max_running": st["max_running"],
+                          "latency_ms_p50": round(sm.latency_p50_us / 1e3, 3)},
+            "q": "one int64 Q histogram resident on the device across every served fill"}
+
+
 # ----------------------------------------------------------------------------- reference arm (oracle)
 def bench_reference(args, ws, rank, local):
     if rank != 0:
@@ -494,6 +581,11 @@ def main():
     ap.add_argument("--quick", action="store_true", help="main measurement only (no plain or batched form)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-fill batched form")
     ap.add_argument("--batched-steps", type=int, default=30)
+    ap.add_argument("--no-served", action="store_true", help="skip the served (request loop) form")
+    ap.add_argument("--serve-pool", type=int, default=4, help="distinct device fills the served stream cycles over")
+    ap.add_argument("--serve-fills", type=int, default=1024, help="fills per served run at 10x and 100x")
+    ap.add_argument("--serve-fills-1x", type=int, default=32, help="fills of the 1x run (1.4 s per 16 fills)")
+    ap.add_argument("--serve-fills-saturated", type=int, default=256)
     ap.add_argument("--calos", type=int, default=24, help="calorimeters per fill (24; fewer only for profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

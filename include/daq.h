@@ -310,6 +310,151 @@ int daq_batch_plan_tuning(const daq_batch_plan *plan, daq_tune_result *out);
 int daq_batch_plan_destroy(daq_batch_plan *plan);
 void daq_tune_cache_clear(void);
 
+/*
+ * Serving: a request loop that admits fills as they arrive (Sec. 3: fills
+ * reach the GPU one after another during each accelerator cycle, and the Q
+ * histograms are summed fill by fill).  A worker thread inside the server
+ * admits every request whose arrival time has come as soon as a slot is free,
+ * enqueues it on one of several streams, so that fills in flight overlap on
+ * the device, and retires fills as their work completes.
+ *
+ *   slot   device memory for one fill: island records, pool rows, pedestals,
+ *          counts, scratch workspace and (DAQ_SERVER_HOST_INPUT) an input
+ *          buffer.  The server carves n_slots slots out of one allocation of
+ *          at most mem_budget_bytes made at creation; a request waits in the
+ *          queue while every slot is busy (admission against the budget).
+ *   Q      one resident histogram (layout of daq_q_bins) that every fill adds
+ *          to; the integer sums make the result independent of the order and
+ *          overlap of fills.
+ *   clock  microseconds since daq_server_create on the host's steady clock.
+ *          Start and completion times come from CUDA events mapped onto that
+ *          clock (re-anchored while the server is idle).
+ *
+ * daq_server_config fields:
+ *   n_calo, n_xtal, n_samples  shape of every fill (row pitch n_samples).
+ *   params          method parameters as for daq_process_fills (threshold,
+ *                   windows, ped_samples, decimation, tile, grid); stream,
+ *                   workspace, events, trace and fill_len are ignored.
+ *   mem_budget_bytes  device bytes the slots may take (> 0).
+ *   max_slots       upper bound on slots (0 = 64).
+ *   n_streams       streams fills are spread over (0 = 4, at most 16).
+ *   hdr_cap, pool_row_cap  per-fill output capacity (0 = worst case:
+ *                   n_calo * n_samples rows, half that plus n_calo + 1 records).
+ *   flags           DAQ_SERVER_HOST_INPUT: requests may name host samples,
+ *                   copied into the slot's input buffer (page-locked memory
+ *                   gives full speed); DAQ_SERVER_AUTO_RELEASE: a slot is freed
+ *                   as soon as its fill completes (only counts and timings are
+ *                   kept; for streaming without reading islands).
+ *   qhist           device int64 Q histogram (caller-owned, accumulated), or
+ *                   NULL for one owned by the server (zeroed at creation).
+ */
+#define DAQ_SERVER_HOST_INPUT 1u
+#define DAQ_SERVER_AUTO_RELEASE 2u
+
+typedef struct daq_server daq_server;
+
+typedef struct daq_server_config {
+    int32_t n_calo;
+    int32_t n_xtal;
+    int64_t n_samples;
+    daq_params params;
+    size_t mem_budget_bytes;
+    int32_t max_slots;
+    int32_t n_streams;
+    int64_t hdr_cap;
+    int64_t pool_row_cap;
+    uint32_t flags;
+    int32_t reserved;
+    int64_t *qhist;
+} daq_server_config;
+
+/* Fill states */
+#define DAQ_FILL_QUEUED 0
+#define DAQ_FILL_RUNNING 1
+#define DAQ_FILL_DONE 2
+#define DAQ_FILL_RELEASED 3
+
+/* Timing and size record of one fill (server clock, microseconds). */
+typedef struct daq_fill_record {
+    int64_t ticket;
+    int64_t n_islands;
+    int64_t n_rows;
+    int64_t raw_bytes;   /* n_calo * n_xtal * fill_len * 2 */
+    double t_arrival;    /* arrival (as submitted) */
+    double t_admit;      /* slot granted and work enqueued (host) */
+    double t_start;      /* work started on the GPU */
+    double t_done;       /* work finished on the GPU */
+    int32_t status;      /* daq_status of the fill */
+    int32_t slot;
+} daq_fill_record;
+
+/* Result of one fill: its record plus device pointers into its slot (valid
+ * until daq_server_release; NULL after AUTO_RELEASE). */
+typedef struct daq_fill_result {
+    daq_fill_record rec;
+    int32_t state;
+    int32_t reserved;
+    const daq_island *hdr;
+    const int16_t *pool;
+    const int32_t *pedestal;
+} daq_fill_result;
+
+typedef struct daq_server_stats {
+    int64_t submitted, admitted, completed, released, failed;
+    int64_t queued, running, max_running;
+    int32_t n_slots, n_streams;
+    size_t slot_bytes, mem_bytes;
+} daq_server_stats;
+
+/* Latency / deadtime summary of completed fills (host arithmetic only). */
+typedef struct daq_serving_summary {
+    int64_t n;              /* fills summarised */
+    double latency_p50_us;  /* t_done - t_arrival, percentiles with linear interpolation */
+    double latency_p99_us;
+    double latency_max_us;
+    double deadtime;        /* over fills in arrival order that have a next fill: the fraction not
+                               done before the next one arrives (0 when n < 2) */
+    double gbs;             /* raw bytes / (last t_done - first t_arrival) / 1e3 (GB/s) */
+    double span_us;
+} daq_serving_summary;
+
+/* Create the server: validates the configuration (DAQ_EINVAL before any GPU
+ * work when invalid, or when the budget holds no slot), allocates the slots on
+ * the current device and starts the worker thread. */
+int daq_server_create(const daq_server_config *cfg, daq_server **out);
+/* Queue one fill.  samples: device (or, with DAQ_SERVER_HOST_INPUT and
+ * on_host != 0, host) int16[n_calo][n_xtal][n_samples]; it must stay valid and
+ * unchanged until the fill completes.  fill_len in [0, n_samples] (-1 = n_samples).
+ * arrival_us: server-clock arrival time; a future time holds the request until
+ * then (replay), < 0 means now.  *ticket receives the fill's ticket (>= 1). */
+int daq_server_submit(daq_server *s, const int16_t *samples, int on_host, int32_t fill_len, double arrival_us,
+                      int64_t *ticket);
+/* Non-blocking state of a ticket (DAQ_EINVAL for an unknown ticket). */
+int daq_server_poll(daq_server *s, int64_t ticket, daq_fill_result *out);
+/* Wait (up to timeout_s seconds) until the ticket is done; DAQ_ETIMEOUT otherwise. */
+int daq_server_wait(daq_server *s, int64_t ticket, double timeout_s, daq_fill_result *out);
+/* Copy a done (not yet released) fill's results to host buffers: up to
+ * hdr_cap island records, pool_cap pool rows and (if ped_host != NULL)
+ * n_calo x n_xtal pedestals.  Synchronous; DAQ_EINVAL unless the fill is done. */
+int daq_server_fetch(daq_server *s, int64_t ticket, daq_island *hdr_host, int64_t hdr_cap, int16_t *pool_host,
+                     int64_t pool_cap, int32_t *ped_host);
+/* Free a done fill's slot. */
+int daq_server_release(daq_server *s, int64_t ticket);
+/* Wait (up to timeout_s) until nothing is queued or running. */
+int daq_server_drain(daq_server *s, double timeout_s);
+int daq_server_get_stats(daq_server *s, daq_server_stats *out);
+/* Copy up to cap records of completed fills, in completion order; *n receives
+ * how many exist.  clear != 0 forgets them afterwards. */
+int daq_server_records(daq_server *s, daq_fill_record *out, int64_t cap, int64_t *n, int clear);
+/* The resident Q histogram (device). */
+int64_t *daq_server_qhist(daq_server *s);
+/* Current server-clock time (microseconds). */
+double daq_server_now_us(daq_server *s);
+/* Stop the worker (after the work in flight completes) and free everything. */
+int daq_server_destroy(daq_server *s);
+/* Summarise records (any order): latency percentiles, deadtime, throughput. */
+int daq_serving_summarize(const daq_fill_record *recs, int64_t n, daq_serving_summary *out);
+
 /* Upper bound on the tiles of a call with these sizes and parameters (rows of
  * the trace buffer); 0 on invalid arguments. */
 int64_t daq_trace_tiles(int n_calo, int n_xtal, int64_t n_samples, int n_fills, const daq_params *params);

@@ -53,6 +53,40 @@ class DaqTuneResult(ctypes.Structure):
 
 
 DAQ_TUNE, DAQ_TUNE_FORCE = 1, 2
+DAQ_SERVER_HOST_INPUT, DAQ_SERVER_AUTO_RELEASE = 1, 2
+DAQ_FILL_QUEUED, DAQ_FILL_RUNNING, DAQ_FILL_DONE, DAQ_FILL_RELEASED = 0, 1, 2, 3
+
+
+class DaqServerConfig(ctypes.Structure):
+    _fields_ = [("n_calo", ctypes.c_int32), ("n_xtal", ctypes.c_int32), ("n_samples", ctypes.c_int64),
+                ("params", DaqParams), ("mem_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32),
+                ("n_streams", ctypes.c_int32), ("hdr_cap", ctypes.c_int64), ("pool_row_cap", ctypes.c_int64),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32), ("qhist", ctypes.c_void_p)]
+
+
+class DaqFillRecord(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("n_islands", ctypes.c_int64), ("n_rows", ctypes.c_int64),
+                ("raw_bytes", ctypes.c_int64), ("t_arrival", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double), ("status", ctypes.c_int32),
+                ("slot", ctypes.c_int32)]
+
+
+class DaqFillResult(ctypes.Structure):
+    _fields_ = [("rec", DaqFillRecord), ("state", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("hdr", ctypes.c_void_p), ("pool", ctypes.c_void_p), ("pedestal", ctypes.c_void_p)]
+
+
+class DaqServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("released", ctypes.c_int64), ("failed", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("running", ctypes.c_int64), ("max_running", ctypes.c_int64), ("n_slots", ctypes.c_int32),
+                ("n_streams", ctypes.c_int32), ("slot_bytes", ctypes.c_size_t), ("mem_bytes", ctypes.c_size_t)]
+
+
+class DaqServingSummary(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("latency_p50_us", ctypes.c_double), ("latency_p99_us", ctypes.c_double),
+                ("latency_max_us", ctypes.c_double), ("deadtime", ctypes.c_double), ("gbs", ctypes.c_double),
+                ("span_us", ctypes.c_double)]
 
 
 class DaqError(RuntimeError):
@@ -110,6 +144,32 @@ def lib():
             L.daq_batch_plan_destroy.restype = i32
             L.daq_tune_cache_clear.argtypes = []
             L.daq_tune_cache_clear.restype = None
+            L.daq_server_create.argtypes = [ctypes.POINTER(DaqServerConfig), ctypes.POINTER(vp)]
+            L.daq_server_create.restype = i32
+            L.daq_server_submit.argtypes = [vp, vp, i32, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(i64)]
+            L.daq_server_submit.restype = i32
+            L.daq_server_poll.argtypes = [vp, i64, ctypes.POINTER(DaqFillResult)]
+            L.daq_server_poll.restype = i32
+            L.daq_server_wait.argtypes = [vp, i64, ctypes.c_double, ctypes.POINTER(DaqFillResult)]
+            L.daq_server_wait.restype = i32
+            L.daq_server_fetch.argtypes = [vp, i64, vp, i64, vp, i64, vp]
+            L.daq_server_fetch.restype = i32
+            L.daq_server_release.argtypes = [vp, i64]
+            L.daq_server_release.restype = i32
+            L.daq_server_drain.argtypes = [vp, ctypes.c_double]
+            L.daq_server_drain.restype = i32
+            L.daq_server_get_stats.argtypes = [vp, ctypes.POINTER(DaqServerStats)]
+            L.daq_server_get_stats.restype = i32
+            L.daq_server_records.argtypes = [vp, ctypes.POINTER(DaqFillRecord), i64, ctypes.POINTER(i64), i32]
+            L.daq_server_records.restype = i32
+            L.daq_server_qhist.argtypes = [vp]
+            L.daq_server_qhist.restype = vp
+            L.daq_server_now_us.argtypes = [vp]
+            L.daq_server_now_us.restype = ctypes.c_double
+            L.daq_server_destroy.argtypes = [vp]
+            L.daq_server_destroy.restype = i32
+            L.daq_serving_summarize.argtypes = [ctypes.POINTER(DaqFillRecord), i64, ctypes.POINTER(DaqServingSummary)]
+            L.daq_serving_summarize.restype = i32
             _lib = L
     return _lib
 
@@ -325,6 +385,176 @@ class BatchPlan:
         if getattr(self, "_h", None):
             daq_batch_plan_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------- serving (same names as the C ABI)
+def daq_server_create(cfg: DaqServerConfig):
+    """Returns (status, server handle or None)."""
+    h = ctypes.c_void_p()
+    rc = lib().daq_server_create(ctypes.byref(cfg), ctypes.byref(h))
+    return int(rc), h.value
+
+
+def daq_server_submit(server, samples_ptr: int, on_host: bool, fill_len: int, arrival_us: float):
+    t = ctypes.c_int64(0)
+    rc = lib().daq_server_submit(server, samples_ptr, int(bool(on_host)), int(fill_len), float(arrival_us),
+                                 ctypes.byref(t))
+    return int(rc), int(t.value)
+
+
+def daq_server_poll(server, ticket: int):
+    r = DaqFillResult()
+    rc = lib().daq_server_poll(server, int(ticket), ctypes.byref(r))
+    return int(rc), r
+
+
+def daq_server_wait(server, ticket: int, timeout_s: float):
+    r = DaqFillResult()
+    rc = lib().daq_server_wait(server, int(ticket), float(timeout_s), ctypes.byref(r))
+    return int(rc), r
+
+
+def daq_server_release(server, ticket: int) -> int:
+    return int(lib().daq_server_release(server, int(ticket)))
+
+
+def daq_server_drain(server, timeout_s: float) -> int:
+    return int(lib().daq_server_drain(server, float(timeout_s)))
+
+
+def daq_server_get_stats(server) -> DaqServerStats:
+    st = DaqServerStats()
+    rc = lib().daq_server_get_stats(server, ctypes.byref(st))
+    if rc:
+        raise DaqError(rc, "daq_server_get_stats")
+    return st
+
+
+def daq_server_records(server, clear: bool = False) -> list:
+    n = ctypes.c_int64(0)
+    lib().daq_server_records(server, None, 0, ctypes.byref(n), 0)
+    buf = (DaqFillRecord * max(1, n.value))()
+    m = ctypes.c_int64(0)
+    rc = lib().daq_server_records(server, buf, n.value, ctypes.byref(m), int(bool(clear)))
+    if rc:
+        raise DaqError(rc, "daq_server_records")
+    return [buf[i] for i in range(min(n.value, m.value))]
+
+
+def daq_server_destroy(server) -> int:
+    return int(lib().daq_server_destroy(server))
+
+
+def daq_serving_summarize(records) -> DaqServingSummary:
+    n = len(records)
+    arr = (DaqFillRecord * max(1, n))(*records)
+    out = DaqServingSummary()
+    rc = lib().daq_serving_summarize(arr, n, ctypes.byref(out))
+    if rc:
+        raise DaqError(rc, "daq_serving_summarize")
+    return out
+
+
+def record_dict(r: DaqFillRecord) -> dict:
+    return {k: getattr(r, k) for k, _ in DaqFillRecord._fields_}
+
+
+class DaqServer:
+    """Request loop over fills of one shape (daq_server_*), Q resident in a
+    caller-visible torch tensor."""
+
+    def __init__(self, n_calo: int, n_xtal: int, n_samples: int, budget_bytes: int, threshold=30, pre=8, post=24,
+                 ped_samples=100, decim=(32,), tile=0, grid=0, max_slots=0, n_streams=0, hdr_cap=0, pool_cap=0,
+                 host_input=False, auto_release=False, device=None, q=None):
+        import torch
+        self.torch = torch
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.device = dev
+        self.shape = (int(n_calo), int(n_xtal), int(n_samples))
+        self.q = q if q is not None else torch.zeros(max(1, q_size(n_calo, n_samples, decim)), dtype=torch.int64,
+                                                     device=dev)
+        cfg = DaqServerConfig()
+        cfg.n_calo, cfg.n_xtal, cfg.n_samples = self.shape
+        cfg.params = make_params(threshold, pre, post, ped_samples, decim, 0, None, 0, tile, grid)
+        cfg.mem_budget_bytes = int(budget_bytes)
+        cfg.max_slots, cfg.n_streams = int(max_slots), int(n_streams)
+        cfg.hdr_cap, cfg.pool_row_cap = int(hdr_cap), int(pool_cap)
+        cfg.flags = (DAQ_SERVER_HOST_INPUT if host_input else 0) | (DAQ_SERVER_AUTO_RELEASE if auto_release else 0)
+        cfg.qhist = self.q.data_ptr() if decim else None
+        with torch.cuda.device(dev):
+            rc, h = daq_server_create(cfg)
+        if rc != DAQ_OK:
+            raise DaqError(rc, "daq_server_create")
+        self._h = h
+        self._inputs = {}   # ticket -> tensor kept alive until the fill is done
+
+    def now_us(self) -> float:
+        return float(lib().daq_server_now_us(self._h))
+
+    def submit(self, samples, fill_len: int = -1, arrival_us: float = -1.0) -> int:
+        """samples: CUDA (or, with host_input, CPU) int16 tensor [C][X][N] (or [1][C][X][N])."""
+        on_host = not samples.is_cuda
+        rc, t = daq_server_submit(self._h, samples.data_ptr(), on_host, fill_len, arrival_us)
+        if rc != DAQ_OK:
+            raise DaqError(rc, "daq_server_submit")
+        self._inputs[t] = samples
+        return t
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> dict:
+        rc, r = daq_server_wait(self._h, ticket, timeout_s)
+        if rc != DAQ_OK:
+            raise DaqError(rc, "daq_server_wait")
+        self._inputs.pop(ticket, None)
+        return dict(record_dict(r.rec), state=r.state)
+
+    def poll(self, ticket: int) -> dict:
+        rc, r = daq_server_poll(self._h, ticket)
+        if rc != DAQ_OK:
+            raise DaqError(rc, "daq_server_poll")
+        return dict(record_dict(r.rec), state=r.state)
+
+    def fetch(self, ticket: int):
+        """(islands ISLAND_DTYPE[n], pool int16[rows][X], pedestal int32[C][X]) of a done fill."""
+        r = self.poll(ticket)
+        C, X, _ = self.shape
+        hdr = np.empty(max(1, r["n_islands"]), ISLAND_DTYPE)
+        pool = np.empty((max(1, r["n_rows"]), X), np.int16)
+        ped = np.empty((C, X), np.int32)
+        rc = lib().daq_server_fetch(self._h, int(ticket), hdr.ctypes.data, r["n_islands"], pool.ctypes.data,
+                                    r["n_rows"], ped.ctypes.data)
+        if rc != DAQ_OK:
+            raise DaqError(rc, "daq_server_fetch")
+        return hdr[: r["n_islands"]], pool[: r["n_rows"]], ped
+
+    def release(self, ticket: int) -> None:
+        rc = daq_server_release(self._h, ticket)
+        if rc != DAQ_OK:
+            raise DaqError(rc, "daq_server_release")
+
+    def drain(self, timeout_s: float = 120.0) -> None:
+        rc = daq_server_drain(self._h, timeout_s)
+        if rc != DAQ_OK:
+            raise DaqError(rc, "daq_server_drain")
+        self._inputs.clear()
+
+    def stats(self) -> dict:
+        st = daq_server_get_stats(self._h)
+        return {k: getattr(st, k) for k, _ in DaqServerStats._fields_}
+
+    def records(self, clear: bool = False) -> list:
+        return daq_server_records(self._h, clear)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            daq_server_destroy(self._h)
+            self._h = None
+            self._inputs.clear()
 
     def __del__(self):
         try:
