@@ -357,10 +357,16 @@ def bench_gb300(args, ws, rank, local):
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         ems = float(te.item())
         d2h = 32 + int(counts_h[0]) * 24 + int(counts_h[1]) * X * 2
+        bw = copy_bandwidth(torch, dev, host, samples, pool_h, out.pool, int(counts_h[1]))
+        e2e_bound = raw_bytes / max(raw_bytes / bw["h2d_gbs"], d2h / bw["d2h_gbs"],
+                                    (raw_bytes + d2h) / bw["bidir_gbs"]) if bw["h2d_gbs"] else None
         result["e2e"] = {"value": round(Ke * raw_bytes * ws / (ems * 1e-3) / 1e9, 2), "unit": UNIT,
                          "h2d_bytes_per_step": raw_bytes, "d2h_bytes_per_step": d2h, "steps": Ke,
                          "ms_per_step": round(ems / Ke, 3),
-                         "api": "daq_process_fills_host (pinned host buffers)"}
+                         "api": "daq_process_fills_host (pinned host buffers; copy-in, processing and copy-out "
+                                "pipelined over calorimeter chunks)",
+                         "copy_bandwidth": bw,
+                         "bound_gbs": None if e2e_bound is None else round(e2e_bound, 2)}
 
     # ---- CPU baseline: the oracle on a bounded sample of the same fill (rank 0)
     if rank == 0 and not args.no_cpu_baseline:
@@ -437,6 +443,52 @@ def bench_batched(args, torch, dev, daq, synth, W) -> dict:
     del samples, out, q
     torch.cuda.empty_cache()
     return res
+
+
+def copy_bandwidth(torch, dev, host_in, dev_in, host_out, dev_out, out_rows: int, reps: int = 3) -> dict:
+    """Pinned host<->device copy rates of this machine (the bound of the end-to-end
+    form): the input host->device, the pool rows device->host, and both at once
+    on two streams.  Plain cudaMemcpyAsync through torch."""
+    a, b = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    src_h, dst_d = host_in.view(-1), dev_in.view(-1)
+    n_out = max(1, out_rows) * dev_out.shape[1]
+    src_d, dst_h = dev_out.view(-1)[:n_out], host_out.view(-1)[:n_out]
+    nb_in, nb_out = src_h.numel() * 2, n_out * 2
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = None
+        for _ in range(reps):
+            e0.record(torch.cuda.current_stream(dev))
+            fn()
+            for st in (a, b):
+                torch.cuda.current_stream(dev).wait_stream(st)
+            e1.record(torch.cuda.current_stream(dev))
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return best
+
+    def h2d():
+        a.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(a):
+            dst_d.copy_(src_h, non_blocking=True)
+
+    def d2h():
+        b.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(b):
+            dst_h.copy_(src_d, non_blocking=True)
+
+    def both():
+        h2d()
+        d2h()
+
+    t_in, t_out, t_both = timed(h2d), timed(d2h), timed(both)
+    return {"h2d_gbs": round(nb_in / (t_in * 1e-3) / 1e9, 1), "d2h_gbs": round(nb_out / (t_out * 1e-3) / 1e9, 1),
+            "bidir_gbs": round((nb_in + nb_out) / (t_both * 1e-3) / 1e9, 1),
+            "method": "best of 3 pinned cudaMemcpyAsync of the fill (h2d) and of its pool rows (d2h), "
+                      "alone and concurrently on two streams"}
 
 
 def burst_schedule(n_fills: int, speed: float, t0_us: float) -> list:

@@ -104,6 +104,13 @@ typedef struct daq_island {
  *   trace        NULL, or device uint64[max_tiles][DAQ_TRACE_WORDS] (max_tiles
  *                from daq_trace_tiles()): per-tile %globaltimer stamps of each
  *                stage (profiling only; costs a few stores per tile).
+ *   calo_base    added to the calorimeter index in island records and in the
+ *                Q rows the call adds to (>= 0), so that a call over a group of
+ *                calorimeters of a larger array writes their true indices.
+ *   q_calos      calorimeters in the qhist_inout array (0 = n_calo); calo_base
+ *                + n_calo must not exceed it (so calo_base > 0 needs q_calos).
+ *                Calorimeter c of the call adds to row calo_base + c of each
+ *                decimation's block of q_calos rows.
  */
 typedef struct daq_params {
     int32_t threshold;
@@ -117,12 +124,14 @@ typedef struct daq_params {
     uint32_t flags;
     int32_t tile;
     int32_t grid;
-    int32_t reserved;
+    int32_t calo_base;
     void *stream;
     void *workspace;
     size_t workspace_bytes;
     void *const *events;
     uint64_t *trace;
+    int32_t q_calos;
+    int32_t reserved;
 } daq_params;
 
 #define DAQ_N_EVENTS 5
@@ -169,8 +178,9 @@ int daq_workspace_size(int n_calo, int n_xtal, int64_t n_samples, int n_fills, c
 
 /*
  * Bins per calorimeter of the Q histogram for decimation factor D:
- * ceil(n_samples / D).  qhist_inout holds n_calo x bins(decim[0]) int64 values,
- * followed (if n_decim == 2) by n_calo x bins(decim[1]).
+ * ceil(n_samples / D).  qhist_inout holds Q x bins(decim[0]) int64 values,
+ * followed (if n_decim == 2) by Q x bins(decim[1]), Q = params->q_calos, or
+ * n_calo when that is 0.
  */
 int64_t daq_q_bins(int64_t n_samples, int32_t decim);
 
@@ -215,11 +225,28 @@ typedef struct daq_host_io {
 /*
  * End-to-end form over host buffers, as the paper's GPU thread does it (Sec. 3:
  * copy one fill to the GPU, process it, return the chopped islands to host
- * memory).  Copies io->samples_host to io->samples_dev on params->stream, runs
- * daq_process_fills with the device outputs in islands_dev, then copies the
- * counts, island records, pool rows and (if requested) pedestals back.  The Q
- * histograms stay on the device (qhist_inout).  Waits for the stream before
- * returning; returns the call's status (DAQ_ECAPACITY if a device or host
+ * memory).  The call is cut into chunks of calorimeter-fills that are
+ * pipelined: the copy of io->samples_host into io->samples_dev for one chunk
+ * overlaps the processing of the previous chunk on params->stream and the
+ * device-to-host copy of earlier chunks' island records and pool rows (exact
+ * sizes).  On return, io->counts_host holds the call's counts and the host
+ * buffers hold the records (in (fill, calo, start) order, pool_row indexing
+ * pool_host), the pool rows and (if requested) the pedestals, exactly as
+ * daq_process_fills would produce them.  The Q histograms stay on the device
+ * (qhist_inout) and accumulate as with daq_process_fills.
+ *   islands_dev  device buffers used as the chunks' working space: with
+ *                capacity for every sample marked (pool_row_cap >= n_fills *
+ *                n_calo * n_samples plus 8 rows per chunk, hdr_cap >= that
+ *                many calorimeter-fills times ceil(n_samples / 2)) the call is
+ *                pipelined, else it runs as one chunk.  Their contents after a
+ *                pipelined call are per-chunk regions, not the call's layout;
+ *                counts are reported in io->counts_host.
+ *   params       as for daq_process_fills; params->workspace sized for the
+ *                whole call.
+ * Synchronous: returns when everything is on the host.  The first call on a
+ * device creates two copy streams, events and a small page-locked count
+ * buffer that live until the process exits; calls on one device are
+ * serialised.  Returns the call's status (DAQ_ECAPACITY if a device or host
  * capacity was short: counts_host then holds the sizes needed).
  */
 int daq_process_fills_host(int n_calo, int n_xtal, int64_t n_samples, int n_fills, const daq_params *params,

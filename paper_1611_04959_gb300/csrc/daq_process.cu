@@ -740,6 +740,9 @@ static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, con
     if (p->pre < 0 || p->post < 0 || p->pre + p->post > 512 || p->ped_samples < 1) return DAQ_EINVAL;
     if (p->n_decim < 0 || p->n_decim > 2) return DAQ_EINVAL;
     if (p->grid < -3) return DAQ_EINVAL;
+    if (p->calo_base < 0 || p->q_calos < 0 ||
+        (int64_t)p->calo_base + n_calo > (p->q_calos > 0 ? (int64_t)p->q_calos : (int64_t)n_calo))
+        return DAQ_EINVAL;
     // scan fields: trailing run < 2^30 samples, island count < 2^31
     if (n_samples > ((int64_t)1 << 30) || (int64_t)n_fills * n_calo * n_samples > ((int64_t)1 << 32))
         return DAQ_EUNSUPPORTED;
@@ -900,8 +903,9 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
         if ((reinterpret_cast<uintptr_t>(out->pool) & 15) || (reinterpret_cast<uintptr_t>(out->hdr) & 7))
             return DAQ_EINVAL;
     }
+    const int64_t q_calos = p.q_calos > 0 ? p.q_calos : n_calo;
     int64_t q_total = 0;
-    for (int d = 0; d < p.n_decim; ++d) q_total += q_bins(n_samples, p.decim[d]) * n_calo;
+    for (int d = 0; d < p.n_decim; ++d) q_total += q_bins(n_samples, p.decim[d]) * q_calos;
     if (!skip_q && q_total > 0 && !qhist_inout) return DAQ_EINVAL;
     if (reinterpret_cast<uintptr_t>(out->counts) & 7) return DAQ_EINVAL;
     const WsLayout wl = ws_layout(n_fills, n_calo, pl.max_tiles);
@@ -925,9 +929,10 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
         a.decim[d] = p.decim[d];
         a.qbins[d] = q_bins(n_samples, p.decim[d]);
         a.qoff[d] = qoff;
-        qoff += a.qbins[d] * n_calo;
+        qoff += a.qbins[d] * q_calos;
     }
     a.fill_base = p.fill_base;
+    a.calo_base = p.calo_base;
     a.fill_len = p.fill_len;
     a.flags = p.flags;
     a.hl = pl.hl;
@@ -1059,6 +1064,6 @@ const char *daq_strerror(int status)
     }
 }
 
-int daq_version(void) { return 100; }
+int daq_version(void) { return 101; }
 
 }  // extern "C"

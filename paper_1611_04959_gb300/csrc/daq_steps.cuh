@@ -102,7 +102,7 @@ struct KArgs {
     int32_t threshold, pre, post, ped_samples;
     int32_t n_decim, decim[2];
     int64_t qbins[2], qoff[2];
-    int32_t fill_base;
+    int32_t fill_base, calo_base;
     const int32_t *fill_len;
     uint32_t flags;
     int32_t hl, hr, ew, rs;  // halo left/right, extended width, smem row pitch (bytes) = 2 boxw
@@ -730,7 +730,7 @@ __device__ __forceinline__ void write_headers(const KArgs &a, const TileInfo &T,
         if (idx < a.hdr_cap) {
             daq_island *h = a.hdr + idx;
             h->fill = a.fill_base + T.f;
-            h->calo = T.c;
+            h->calo = a.calo_base + T.c;
             h->start = (int32_t)start;
             h->len = (int32_t)ilen;
             h->pool_row = row_end - ilen + 1;
@@ -750,7 +750,7 @@ __device__ __forceinline__ void q_partial(const KArgs &a, const TileInfo &T, con
     for (int d = 0; d < a.n_decim; ++d) {
         const long long D = a.decim[d];
         unsigned long long *qrow =
-            reinterpret_cast<unsigned long long *>(a.q + a.qoff[d] + (long long)T.c * a.qbins[d]);
+            reinterpret_cast<unsigned long long *>(a.q + a.qoff[d] + (long long)(a.calo_base + T.c) * a.qbins[d]);
         const long long k_lo = T.t0 / D, k_hi = (T.t_end - 1) / D;
         for (long long k = k_lo + gt; k <= k_hi; k += nthr) {
             const long long lo = (k * D > T.t0 ? k * D : T.t0) - T.t0;

@@ -38,8 +38,8 @@ def test_every_declared_symbol_is_exported(daq):
 
 
 def test_struct_layouts_match_header(daq):
-    # daq_params: 8 int32, pointer, uint32 + 3 int32, 2 pointers, size_t, 2 pointers
-    assert ctypes.sizeof(daq.DaqParams) == 32 + 8 + 16 + 8 + 8 + 8 + 8 + 8
+    # daq_params: 8 int32, pointer, uint32 + 3 int32, 2 pointers, size_t, 2 pointers, 2 int32
+    assert ctypes.sizeof(daq.DaqParams) == 32 + 8 + 16 + 8 + 8 + 8 + 8 + 8 + 8
     assert ctypes.sizeof(daq.DaqIslands) == 6 * 8
     assert daq.ISLAND_DTYPE.itemsize == 24
 
@@ -60,7 +60,7 @@ def test_host_calls(daq):
 
 @pytest.mark.parametrize("bad", [
     dict(pre=-1), dict(post=-2), dict(ped_samples=0), dict(decim=(0,)), dict(pre=300, post=300),
-    dict(tile=100), dict(grid=-4),
+    dict(tile=100), dict(grid=-4), dict(calo_base=-1), dict(q_calos=-1), dict(calo_base=1, q_calos=1),
 ])
 def test_bad_parameters_rejected_before_any_device_work(daq, bad):
     kw = dict(threshold=30, pre=8, post=24, ped_samples=100, decim=(32,))
