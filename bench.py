@@ -313,6 +313,10 @@ def bench_gb300(args, ws, rank, local):
     if not args.no_served and not args.quick:
         result["served"] = bench_served(args, torch, dev, daq, synth, W, samples)
 
+    # ---- stress batch: 48 fills (69.67 GB) in one call, output sizes computed on the device
+    if not args.no_stress and not args.quick:
+        result["stress"] = bench_stress(args, torch, dev, daq, synth, W)
+
     # ---- plain form: one CTA per tile, no persistence
     if not args.quick:
         pp, _ = make_p(grid=-1)
@@ -491,6 +495,77 @@ def copy_bandwidth(torch, dev, host_in, dev_in, host_out, dev_out, out_rows: int
                       "alone and concurrently on two streams"}
 
 
+def bench_stress(args, torch, dev, daq, synth, W) -> dict:
+    """The stress workload: 48 fills x 24 calorimeters x 54 x 560,000 int16
+    (69.67 GB device-resident), 10x pulse rate, T=15, post=64, D in {8, 32},
+    one call over all 48 fills; the fills cycle over 4 distinct generated
+    fills (the kernels cannot tell)."""
+    import numpy as np
+    w = W.STRESS
+    params = w.params()
+    F, C, X, N = w.n_fills, w.n_calo, 54, w.n_samples
+    free, _ = torch.cuda.mem_get_info(dev)
+    need = 2 * F * C * X * N * 2 + (8 << 30)
+    if free < need:
+        return {"skipped": f"needs {need / 1e9:.0f} GB free device memory, {free / 1e9:.0f} GB free"}
+    n_distinct = 4
+    t0 = time.perf_counter()
+    x = torch.empty((F, C, X, N), dtype=torch.int16, device=dev)
+    stage = torch.empty((1, C, X, N), dtype=torch.int16).pin_memory()
+    for d in range(n_distinct):
+        synth.generate(w.config(), out=stage.numpy(), n_threads=os.cpu_count() or 1, fills=(d, 1))
+        x[d].copy_(stage[0])
+    for f in range(n_distinct, F):
+        x[f].copy_(x[f % n_distinct])
+    del stage
+    gen_s = time.perf_counter() - t0
+    raw = F * C * X * N * 2
+    out = daq.Outputs(torch, dev, F, C, X, F * C * 1024, F * C * N)
+    q = torch.zeros(daq.q_size(C, N, params["decim"]), dtype=torch.int64, device=dev)
+    stream = torch.cuda.Stream(dev)
+    p = daq.make_params(**params, stream=stream)
+    wsb = daq.daq_workspace_size(C, X, N, F, p)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    p.workspace, p.workspace_bytes = ws.data_ptr(), wsb
+    isl = out.struct()
+    for _ in range(2):
+        rc = daq.daq_process_fills(x.data_ptr(), C, X, N, F, p, isl, q.data_ptr())
+        assert rc == daq.DAQ_OK, rc
+    torch.cuda.synchronize(dev)
+    counts = out.counts.cpu().numpy()
+    status = daq.daq_status_from_counts(counts)
+    Ks = max(3, min(args.steps, args.stress_steps))
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(Ks)]
+    for row in evs:
+        for e in row:
+            e.record(stream)
+    arrs = [(ctypes.c_void_p * 5)(*[e.cuda_event for e in row]) for row in evs]
+    torch.cuda.synchronize(dev)
+    for k in range(Ks):
+        p.events = ctypes.cast(arrs[k], ctypes.c_void_p).value
+        daq.daq_process_fills(x.data_ptr(), C, X, N, F, p, isl, q.data_ptr())
+    torch.cuda.synchronize(dev)
+    ms = [r[0].elapsed_time(r[4]) for r in evs]
+    total = evs[0][0].elapsed_time(evs[-1][4])
+    kern = {name: round(statistics.fmean(r[i].elapsed_time(r[i + 1]) for r in evs), 3)
+            for i, name in enumerate(["daq_prepare_kernel", "daq_count_kernel", "daq_scan_kernels",
+                                      "daq_compact_kernel"])}
+    res = {"value": round(Ks * raw / (total * 1e-3) / 1e9, 2), "unit": UNIT, "steps": Ks,
+           "ms_per_batch": round(total / Ks, 3), "latency_ms_p99": round(float(np.percentile(ms, 99)), 3),
+           "pct_of_hbm_peak": round(100.0 * Ks * raw / (total * 1e-3) / 1e9 / measured_peaks()[0], 2),
+           "workload": "48 fills x 24 calorimeters x 54 crystals x 560,000 int16 (69.67 GB device-resident), "
+                       "10x pulse rate (~15,000 pulses per calorimeter-fill), T=15, pre=8, post=64, D=8 and 32; "
+                       "fills cycle over 4 distinct generated fills",
+           "raw_bytes_per_batch": raw, "islands_per_batch": int(counts[0]), "pool_rows_per_batch": int(counts[1]),
+           "coverage": round(int(counts[1]) / (F * C * N), 6), "status": status,
+           "output_sizes": "computed on the device (counts) in the same call", "gpu_launches": 5 * Ks,
+           "kernels_ms": kern,
+           "generation_s": round(gen_s, 1)}
+    del x, out, q, ws
+    torch.cuda.empty_cache()
+    return res
+
+
 def burst_schedule(n_fills: int, speed: float, t0_us: float) -> list:
     """Arrival times (us) of the accelerator cycle replayed `speed` times
     faster: bursts of 8 fills 10 ms apart, two bursts per 1.4 s cycle (the
@@ -634,6 +709,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-fill batched form")
     ap.add_argument("--batched-steps", type=int, default=30)
     ap.add_argument("--no-served", action="store_true", help="skip the served (request loop) form")
+    ap.add_argument("--no-stress", action="store_true", help="skip the 48-fill (69.67 GB) stress batch")
+    ap.add_argument("--stress-steps", type=int, default=10)
     ap.add_argument("--serve-pool", type=int, default=4, help="distinct device fills the served stream cycles over")
     ap.add_argument("--serve-fills", type=int, default=1024, help="fills per served run at 10x and 100x")
     ap.add_argument("--serve-fills-1x", type=int, default=32, help="fills of the 1x run (1.4 s per 16 fills)")
