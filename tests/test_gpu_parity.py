@@ -181,3 +181,12 @@ def test_full_fill_24_calorimeters(env):
     w = W.PLAIN_FULL_FILL
     s = env["synth"].generate(w.config())
     compare(env, s, w.params(), n_threads=16)
+
+
+def test_sparse_regime(env):
+    """Per-crystal noise 3/sqrt(54): islands cover ~8% of the fill."""
+    from synth import workloads as W
+    w = W.scaled(W.SPARSE_FULL_FILL, n_calo=3)
+    s = env["synth"].generate(w.config())
+    res, ref = compare(env, s, w.params())
+    assert 0.02 < ref["n_rows"] / (3 * s.shape[3]) < 0.2
