@@ -92,7 +92,10 @@ typedef struct daq_island {
  *                > 0 = two-pass form with exactly this many CTAs per kernel;
  *                -1 = single-pass plain kernel, one CTA per tile;
  *                -2 = single-pass plain kernel, persistent;
- *                -3 = single-pass pipelined kernel (one CTA per SM, warp roles).
+ *                -3 = single-pass pipelined kernel (one CTA per SM, warp roles);
+ *                -4 = single-launch form: the two passes in one cooperative
+ *                     launch, the compact role a bounded distance behind the
+ *                     count role so that its re-read hits L2.
  *   stream       cudaStream_t (NULL = legacy default stream).
  *   workspace    device scratch of at least daq_workspace_size() bytes,
  *                16-byte aligned; reused by the call and not to be shared by
@@ -107,6 +110,8 @@ typedef struct daq_island {
  *   calo_base    added to the calorimeter index in island records and in the
  *                Q rows the call adds to (>= 0), so that a call over a group of
  *                calorimeters of a larger array writes their true indices.
+ *   lag_tiles    single-launch form (grid -4): tiles the count role may run
+ *                ahead of the compact role (0 = 1024; at least 640).
  *   q_calos      calorimeters in the qhist_inout array (0 = n_calo); calo_base
  *                + n_calo must not exceed it (so calo_base > 0 needs q_calos).
  *                Calorimeter c of the call adds to row calo_base + c of each
@@ -131,7 +136,7 @@ typedef struct daq_params {
     void *const *events;
     uint64_t *trace;
     int32_t q_calos;
-    int32_t reserved;
+    int32_t lag_tiles;
 } daq_params;
 
 #define DAQ_N_EVENTS 5

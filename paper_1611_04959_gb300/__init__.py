@@ -34,7 +34,7 @@ class DaqParams(ctypes.Structure):
                 ("tile", ctypes.c_int32), ("grid", ctypes.c_int32), ("calo_base", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("events", ctypes.c_void_p), ("trace", ctypes.c_void_p),
-                ("q_calos", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("q_calos", ctypes.c_int32), ("lag_tiles", ctypes.c_int32)]
 
 
 class DaqIslands(ctypes.Structure):
@@ -263,7 +263,8 @@ def daq_status_from_counts(counts_host) -> int:
 
 # ------------------------------------------------------------------- torch marshalling helpers
 def make_params(threshold=30, pre=8, post=24, ped_samples=100, decim=(32,), fill_base=0, fill_len=None,
-                flags=0, tile=0, grid=0, stream=None, workspace=None, calo_base=0, q_calos=0) -> DaqParams:
+                flags=0, tile=0, grid=0, stream=None, workspace=None, calo_base=0, q_calos=0,
+                lag_tiles=0) -> DaqParams:
     p = daq_params_default()
     p.threshold, p.pre, p.post, p.ped_samples = int(threshold), int(pre), int(post), int(ped_samples)
     decim = tuple(decim)
@@ -274,7 +275,7 @@ def make_params(threshold=30, pre=8, post=24, ped_samples=100, decim=(32,), fill
     p.fill_len = None if fill_len is None else int(fill_len.data_ptr())
     p.flags = int(flags)
     p.tile, p.grid = int(tile), int(grid)
-    p.calo_base, p.q_calos = int(calo_base), int(q_calos)
+    p.calo_base, p.q_calos, p.lag_tiles = int(calo_base), int(q_calos), int(lag_tiles)
     p.stream = None if stream is None else int(stream.cuda_stream)
     if workspace is not None:
         p.workspace = int(workspace.data_ptr())
@@ -310,7 +311,8 @@ class Outputs:
 
 def process_fills(samples, threshold=30, pre=8, post=24, ped_samples=100, decim=(32,), fill_len=None,
                   fill_base=0, q=None, outputs: Outputs | None = None, hdr_cap=None, pool_cap=None,
-                  workspace=None, flags=0, tile=0, grid=0, stream=None, sync=True, calo_base=0, q_calos=0) -> dict:
+                  workspace=None, flags=0, tile=0, grid=0, stream=None, sync=True, calo_base=0, q_calos=0,
+                  lag_tiles=0) -> dict:
     """Run the path on a CUDA int16 tensor samples[F][C][X][N].
 
     Allocates (with torch) whatever output the caller did not pass; returns a
@@ -332,7 +334,7 @@ def process_fills(samples, threshold=30, pre=8, post=24, ped_samples=100, decim=
         q = torch.zeros(q_size(q_calos or C, N, decim), dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev) if stream is None else stream
     p = make_params(threshold, pre, post, ped_samples, decim, fill_base, fill_len, flags, tile, grid, stream,
-                    calo_base=calo_base, q_calos=q_calos)
+                    calo_base=calo_base, q_calos=q_calos, lag_tiles=lag_tiles)
     ws_bytes = daq_workspace_size(C, X, N, F, p)
     if workspace is None or workspace.numel() * workspace.element_size() < ws_bytes:
         workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)

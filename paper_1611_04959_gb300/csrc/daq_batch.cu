@@ -53,10 +53,12 @@ struct Candidate {
 };
 
 // Form x tile x CTAs: two-pass at 128 / 224 / 448 with occupancy grids (2 CTAs
-// per SM) and with one CTA per SM; the single-pass forms for comparison.
+// per SM) and with one CTA per SM; the single-launch form at 448 / 224; the
+// single-pass forms for comparison.
 std::vector<Candidate> candidates(int sms)
 {
-    return {{448, 0}, {224, 0}, {128, 0}, {448, sms}, {224, sms}, {448, -1}, {960, -1}, {448, -2}, {448, -3}};
+    return {{448, 0},  {224, 0},  {128, 0},  {448, sms}, {224, sms}, {448, -4},
+            {224, -4}, {448, -1}, {960, -1}, {448, -2},  {448, -3}};
 }
 
 int q_values(int64_t N, int C, const daq_params &p, int64_t *n)

@@ -70,7 +70,7 @@ static WsLayout ws_layout(int64_t n_fills, int64_t n_calo, int64_t max_tiles)
     auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
     WsLayout w;
     w.ticket = 0;
-    w.fts = up(16);
+    w.fts = up(512);  // [0, 16) ticket; 128 and 256: counters of the single-launch form
     w.lens = up(w.fts + sizeof(long long) * (size_t)(n_fills + 1));
     w.ptot = up(w.lens + sizeof(int32_t) * (size_t)(n_fills > 0 ? n_fills : 1));
     w.status = up(w.ptot + sizeof(int32_t) * (size_t)(n_fills * n_calo > 0 ? n_fills * n_calo : 1));
@@ -101,7 +101,12 @@ __global__ void __launch_bounds__(kThreads) daq_prepare_kernel(KArgs a, int tw)
     __shared__ long long s_carry;
     __shared__ long long s_ped[kWarps];
 
-    if (a.mode != kModeTwoPass) {  // scan state of the single-pass kernels
+    if (a.mode == kModeFused) {  // records carry a valid bit; counters restart at 0
+        uint4 *rc = reinterpret_cast<uint4 *>(a.recs);
+        for (long long i = (long long)blockIdx.x * kThreads + tid; i < a.max_tiles; i += (long long)gridDim.x * kThreads)
+            rc[i] = make_uint4(0u, 0u, 0u, 0u);
+        if (blockIdx.x == 0 && tid < 2) a.fctr[16 * tid] = 0ull;
+    } else if (a.mode != kModeTwoPass) {  // scan state of the single-pass kernels
         uint4 *st = reinterpret_cast<uint4 *>(a.status);
         const long long n16 = a.max_tiles * (long long)(sizeof(TileStatus) / 16);
         for (long long i = (long long)blockIdx.x * kThreads + tid; i < n16; i += (long long)gridDim.x * kThreads)
@@ -642,6 +647,11 @@ static DeviceInfo device_info(int dev)
 // Shared memory one CTA may use, for planning before any device is queried
 // (GB300: 227 KB).
 constexpr int kSmemBudget = 227 * 1024;
+// Single-launch form: default and least distance (tiles) the count role may
+// run ahead of the compact role.  The least is the scanner's round (one block
+// of tiles), below which the roles could wait on each other forever.
+constexpr int64_t kFusedLagTiles = 1024;
+constexpr int64_t kFusedMinLag = 2 * kCountThreads;
 
 struct Plan {
     int tw, hl, hr, ew, rs, boxw, nbox, box_stride, slot_bytes, need_sarr, mode;
@@ -699,6 +709,10 @@ static void plan_geometry(Plan *pl, int tw, int pre, int post, int X)
     } else {
         pl->smem = count_smem_bytes(tw, pl->slot_bytes, pl->need_sarr);
         pl->smem_b = compact_smem_bytes(tw, X, pl->slot_bytes_b);
+        if (pl->mode == kModeFused) {  // one kernel holds either role
+            pl->smem = std::max(pl->smem, pl->smem_b);
+            pl->smem_b = 0;
+        }
     }
 }
 
@@ -739,7 +753,8 @@ static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, con
     if (n_xtal > kMaxXtal) return DAQ_EUNSUPPORTED;
     if (p->pre < 0 || p->post < 0 || p->pre + p->post > 512 || p->ped_samples < 1) return DAQ_EINVAL;
     if (p->n_decim < 0 || p->n_decim > 2) return DAQ_EINVAL;
-    if (p->grid < -3) return DAQ_EINVAL;
+    if (p->grid < -4) return DAQ_EINVAL;
+    if (p->lag_tiles < 0) return DAQ_EINVAL;
     if (p->calo_base < 0 || p->q_calos < 0 ||
         (int64_t)p->calo_base + n_calo > (p->q_calos > 0 ? (int64_t)p->q_calos : (int64_t)n_calo))
         return DAQ_EINVAL;
@@ -752,7 +767,8 @@ static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, con
         if (p->decim[d] % 8) pl->need_sarr = 1;
     }
     if (p->tile != 0 && p->tile != 128 && p->tile != 224 && p->tile != 448 && p->tile != 960) return DAQ_EINVAL;
-    pl->mode = p->grid >= 0 ? kModeTwoPass : (p->grid == -3 ? kModePipelined : kModePlain);
+    pl->mode = p->grid >= 0 ? kModeTwoPass
+                            : (p->grid == -3 ? kModePipelined : (p->grid == -4 ? kModeFused : kModePlain));
     const int hl = (p->post + 1 + 7) & ~7, hr = (p->pre + 1 + 7) & ~7;
     const int limit = p->tile ? p->tile : 448;
     int chosen = -1;
@@ -849,6 +865,28 @@ static cudaError_t launch_twopass(const KArgs &a, const Plan &pl, int grid, int 
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (ev && (e = cudaEventRecord(ev[4], s)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+// Single-launch form: one cooperative launch of every CTA that fits (roles by
+// block).  Events [2], [3] and [4] are all recorded after it.
+template <int TW>
+static cudaError_t launch_fused(const KArgs &a, const Plan &pl, int sms, cudaEvent_t const *ev, cudaStream_t s)
+{
+    static size_t conf[64] = {0};
+    cudaError_t e = ensure_smem(daq_fused_kernel<TW>, pl.smem, conf);
+    if (e != cudaSuccess) return e;
+    int per = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, daq_fused_kernel<TW>, kCountThreads, pl.smem);
+    if (e != cudaSuccess) return e;
+    const int grid = per * sms;
+    if (grid < 3) return cudaErrorInvalidConfiguration;
+    void *args[] = {const_cast<KArgs *>(&a)};
+    e = cudaLaunchCooperativeKernel((const void *)daq_fused_kernel<TW>, dim3(grid), dim3(kCountThreads), args,
+                                    pl.smem, s);
+    if (e != cudaSuccess) return e;
+    for (int i = 2; i <= 4; ++i)
+        if (ev && (e = cudaEventRecord(ev[i], s)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -960,6 +998,7 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
                                       pl.boxw_b, n_xtal);
     a.need_sarr = pl.need_sarr;
     a.max_tiles = pl.max_tiles;
+    a.lag_tiles = std::max<int64_t>(p.lag_tiles > 0 ? p.lag_tiles : kFusedLagTiles, kFusedMinLag);
     a.hdr = skip_isl ? nullptr : out->hdr;
     a.hdr_cap = skip_isl ? 0 : out->hdr_cap;
     a.pool = skip_isl ? nullptr : out->pool;
@@ -969,6 +1008,7 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
     a.q = qhist_inout;
     unsigned char *ws = static_cast<unsigned char *>(p.workspace);
     a.ticket = reinterpret_cast<unsigned int *>(ws + wl.ticket);
+    a.fctr = reinterpret_cast<unsigned long long *>(ws + 128);
     a.fill_tile_start = reinterpret_cast<long long *>(ws + wl.fts);
     a.lens = reinterpret_cast<int32_t *>(ws + wl.lens);
     a.ptot = reinterpret_cast<int32_t *>(ws + wl.ptot);
@@ -996,7 +1036,13 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
 
     const int64_t tiles_cap = std::max<int64_t>(1, std::min<int64_t>(pl.max_tiles, INT32_MAX));
     cudaError_t e;
-    if (pl.mode == kModeTwoPass) {
+    if (pl.mode == kModeFused) {
+        switch (pl.tw) {
+        case 128: e = launch_fused<128>(a, pl, di.sms, ev, s); break;
+        case 224: e = launch_fused<224>(a, pl, di.sms, ev, s); break;
+        default: e = launch_fused<448>(a, pl, di.sms, ev, s); break;
+        }
+    } else if (pl.mode == kModeTwoPass) {
         switch (pl.tw) {
         case 128: e = launch_twopass<128>(a, pl, p.grid, di.sms, skip_isl, ev, s); break;
         case 224: e = launch_twopass<224>(a, pl, p.grid, di.sms, skip_isl, ev, s); break;

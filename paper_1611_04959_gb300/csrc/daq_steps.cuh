@@ -22,7 +22,7 @@ namespace daq {
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // bounded device waits (4 s)
 constexpr int kMaxTileWords = 14;                 // marks words of the widest two-pass tile (448 samples)
 // kernels a call may use (daq_params.grid picks one)
-enum : int32_t { kModeTwoPass = 0, kModePlain = 1, kModePipelined = 2 };
+enum : int32_t { kModeTwoPass = 0, kModePlain = 1, kModePipelined = 2, kModeFused = 3 };
 constexpr int kMaxXtal = 64;
 constexpr int kMaxExtBits = 1024;  // tile + halos: one warp of 32-bit words
 
@@ -117,6 +117,10 @@ struct KArgs {
     unsigned long long wpr_mul;  // floor(2^32 / wpr) + 1, for w / wpr (w < 2^16)
     int32_t need_sarr;
     int64_t max_tiles;
+    // single-launch form: tiles the count role may run ahead of the compact
+    // role, and the two progress counters (tiles scanned, tiles compacted)
+    int64_t lag_tiles;
+    unsigned long long *fctr;
     // outputs
     daq_island *hdr;
     int64_t hdr_cap;

@@ -1,4 +1,5 @@
-// Two-pass form of the per-fill processing (the default path).
+// Two-pass form of the per-fill processing (the default path), and its
+// single-launch variant.
 //
 //   daq_count_kernel    every tile once, with its halo: crystal sums, pedestal
 //                       subtraction, threshold, pre/post windows (the marks of
@@ -13,6 +14,11 @@
 //                       memory at the phase of their global position, written
 //                       with one bulk copy (plus unaligned ends), and the tile's
 //                       island records are written.
+//   daq_fused_kernel    the same three steps in one cooperative launch: count
+//                       CTAs publish each tile's aggregate, one scanner CTA turns
+//                       aggregates into prefixes in tile order, compact CTAs
+//                       follow at most lag_tiles tiles behind the count CTAs, so
+//                       the tile they re-read is still in L2.
 #pragma once
 
 #include "daq_steps.cuh"
@@ -26,6 +32,7 @@ constexpr int kScanChunk = kScanThreads * kScanPer;
 struct __align__(16) TileRec {
     int32_t m, s, tr, flags;  // flags: 1 continues (full), 2 mark before the tile, 4 mark after it
 };
+constexpr int32_t kRecValid = 0x100;  // single-launch form: the record has been published
 
 struct __align__(16) TileExcl {
     long long m;  // pool rows before the tile
@@ -97,18 +104,43 @@ struct CountSmem {
     }
 };
 
+// Progress counters of the single-launch form (workspace words).
+__device__ __forceinline__ unsigned long long *scanned_ctr(const KArgs &a) { return a.fctr; }
+__device__ __forceinline__ unsigned long long *compacted_ctr(const KArgs &a) { return a.fctr + 16; }
+
+// Wait until *p >= v (acquire), giving up after the wait limit or when another
+// CTA has flagged a timeout.  One thread.
+__device__ __forceinline__ bool wait_counter_ge(const KArgs &a, const unsigned long long *p, unsigned long long v)
+{
+    if (ld_acquire_u64(p) >= v) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0;; ++i) {
+        __nanosleep(64);
+        if (ld_acquire_u64(p) >= v) return true;
+        if ((i & 63u) == 63u) {
+            if (aborted(a)) return false;
+            if (global_ns() - t0 > kWaitLimitNs) {
+                set_status_bit(a, DAQ_DEV_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
 // Eight sum warps turn a tile into threshold bits and block sums; marks warp
 // s (one per buffer s = j & 1) turns the bits of the CTA's tiles j = s, s + 2,
 // ... into marks words and the tile aggregate and adds the tile's Q bins, while
 // the sum warps go on with the next tile.  Two tile slots are loaded ahead by
 // TMA.  Handoffs (per buffer): full (TMA landed), sums (8 sum warps done: the
 // slot may be refilled and the bits read), marks (bits and block sums read:
-// the buffer may be rewritten).
-template <int TW>
-__global__ void __launch_bounds__(kCountThreads, 2) daq_count_kernel(const __grid_constant__ KArgs a)
+// the buffer may be rewritten).  The CTA takes tiles first, first + G, ...
+// kFused: a tile is loaded only while it is at most lag_tiles ahead of the
+// tiles compacted, and its aggregate is published with a release store and a
+// valid bit for the scanner.
+template <int TW, bool kFused>
+__device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, long long first, long long G)
 {
     constexpr int NWT = TW / 32, NBT = TW / 8;
-    extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned char *slot0 = smem;
     uint8_t *abyte0 = smem + CountSmem::abyte(a.slot_bytes);
@@ -133,11 +165,13 @@ __global__ void __launch_bounds__(kCountThreads, 2) daq_count_kernel(const __gri
     }
     __syncthreads();
     const long long total = plan.fts[a.n_fills];
-    const long long G = gridDim.x;
     const int n_steps = (a.ew + 63) / 64;
     constexpr int kSumThreads = 32 * kCountSumWarps;
 
     auto start_load = [&](long long tile, int s) {  // thread 0
+        if (kFused &&
+            !wait_counter_ge(a, compacted_ctr(a), tile > a.lag_tiles ? (unsigned long long)(tile - a.lag_tiles) : 0ull))
+            return;  // timed out: the sum warps time out on this slot too
         TileInfo &T = tinfo[s];
         decode_tile<TW>(a, tile, T, plan.fts, plan.lens);
         trace_stamp(a, tile, 0);
@@ -153,11 +187,11 @@ __global__ void __launch_bounds__(kCountThreads, 2) daq_count_kernel(const __gri
 
     if (warp < kCountSumWarps) {
         if (tid == 0) {
-            if ((long long)blockIdx.x < total) start_load(blockIdx.x, 0);
-            if ((long long)blockIdx.x + G < total) start_load(blockIdx.x + G, 1);
+            if (first < total) start_load(first, 0);
+            if (first + G < total) start_load(first + G, 1);
         }
         for (long long j = 0;; ++j) {
-            const long long tile = blockIdx.x + j * G;
+            const long long tile = first + j * G;
             if (tile >= total) break;
             const int s = (int)(j & 1);
             const uint32_t par = (uint32_t)((j >> 1) & 1);
@@ -201,12 +235,12 @@ __global__ void __launch_bounds__(kCountThreads, 2) daq_count_kernel(const __gri
                 }
             }
         }
-    } else {
+    } else if (warp < kCountSumWarps + 2) {
         // ------------------------------------------------------------ marks, aggregate, Q bins of buffer s
         const int s = warp - kCountSumWarps;
         const bool skip_q = (a.flags & DAQ_SKIP_Q) != 0;
         for (long long j = s;; j += 2) {
-            const long long tile = blockIdx.x + j * G;
+            const long long tile = first + j * G;
             if (tile >= total) break;
             if (!warp_wait(sums + s, (uint32_t)((j >> 1) & 1))) {
                 if (lane == 0) set_status_bit(a, DAQ_DEV_TIMEOUT);
@@ -219,13 +253,26 @@ __global__ void __launch_bounds__(kCountThreads, 2) daq_count_kernel(const __gri
                                                  TileWords{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
                                                  nullptr, lane);
             if (lane < NWT) a.marks[T.tile * NWT + lane] = Mt;
+            if (kFused) {
+                __threadfence();
+                __syncwarp();
+            }
             if (lane == 0) {
                 TileRec r;
                 r.m = (int32_t)agg.m;
                 r.s = (int32_t)agg.s;
                 r.tr = (int32_t)agg.tr;
                 r.flags = (agg.full ? 1 : 0) | (int)((edges & 1u) << 1) | (int)((edges >> 1) << 2);
-                reinterpret_cast<TileRec *>(a.recs)[T.tile] = r;
+                if (kFused) {
+                    // marks words first, then the record with its valid bit (release)
+                    __threadfence();
+                    const unsigned long long lo = (unsigned long long)(uint32_t)r.m | ((unsigned long long)(uint32_t)r.s << 32);
+                    const unsigned long long hi =
+                        (unsigned long long)(uint32_t)r.tr | ((unsigned long long)(uint32_t)(r.flags | kRecValid) << 32);
+                    st_release_b128(reinterpret_cast<TileRec *>(a.recs) + T.tile, lo, hi);
+                } else {
+                    reinterpret_cast<TileRec *>(a.recs)[T.tile] = r;
+                }
                 trace_stamp(a, T.tile, 4);
             }
             if (!skip_q) q_partial(a, T, blocksum0 + NBT * s, sarr0 + (a.need_sarr ? TW * s : 0), lane, 32);
@@ -233,6 +280,13 @@ __global__ void __launch_bounds__(kCountThreads, 2) daq_count_kernel(const __gri
             if (lane == 0) mbar_arrive(mdone + s);
         }
     }
+}
+
+template <int TW>
+__global__ void __launch_bounds__(kCountThreads, 2) daq_count_kernel(const __grid_constant__ KArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    count_role<TW, false>(a, smem, blockIdx.x, gridDim.x);
 }
 
 // ============================================================================ scan of the aggregates
@@ -393,13 +447,17 @@ __device__ __forceinline__ void plain_tile_load_b(const KArgs &a, const TileInfo
 // One tile slot: the next tile's load is issued as soon as the current tile's
 // rows are staged, so it lands while the pool rows and island records of the
 // current tile are written; the marks, record and prefix of the next tile are
-// loaded into registers at the same point.
-template <int TW>
-__global__ void __launch_bounds__(256, 2) daq_compact_kernel(const __grid_constant__ KArgs a)
+// loaded into registers at the same point.  The CTA takes tiles first, first +
+// G, ...; any block size that is a multiple of 32 and >= 128.
+// kFused: a tile's marks, record and prefix are read once the scanner has
+// passed it (L1-bypassing loads: other CTAs wrote them during this launch), and
+// each tile staged is counted in the compacted counter.
+template <int TW, bool kFused>
+__device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem, long long first, long long G)
 {
     constexpr int NWT = TW / 32;
-    extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nthr = blockDim.x, nwarps = nthr >> 5;
     const int X = a.n_xtal;
     unsigned char *slot = smem;
     unsigned char *stage = slot + a.slot_bytes_b;  // TW rows of 2X bytes, 16-byte phase, + 32
@@ -411,9 +469,9 @@ __global__ void __launch_bounds__(256, 2) daq_compact_kernel(const __grid_consta
     Agg *s_ex = reinterpret_cast<Agg *>(tinfo + 1);
     Agg *s_agg = s_ex + 1;
     uint64_t *bar = reinterpret_cast<uint64_t *>(s_agg + 1);
-    long long *fts_s = reinterpret_cast<long long *>(bar + 1);        // [kPlanSmem + 1]
+    long long *fts_s = reinterpret_cast<long long *>(bar + 1);             // [kPlanSmem + 1]
     int32_t *lens_s = reinterpret_cast<int32_t *>(fts_s + kPlanSmem + 1);  // [kPlanSmem]
-    const PlanView plan = cache_plan(a, fts_s, lens_s, tid, 256);
+    const PlanView plan = cache_plan(a, fts_s, lens_s, tid, nthr);
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
@@ -433,11 +491,25 @@ __global__ void __launch_bounds__(256, 2) daq_compact_kernel(const __grid_consta
             issue_tile_load_b(a, *tinfo, slot, bar);
         }
     };
-    // warp 0's inputs of the next tile, in registers
-    auto load_inputs = [&](long long tile, uint32_t &Mt, TileRec &r, TileExcl &e) {
-        Mt = lane < NWT ? a.marks[tile * NWT + lane] : 0u;
-        r = recs[tile];
-        e = exs[tile];
+    // warp 0's inputs of the next tile, in registers; false if the wait gave up
+    auto load_inputs = [&](long long tile, uint32_t &Mt, TileRec &r, TileExcl &e) -> bool {
+        if (kFused) {
+            int ok = 1;
+            if (lane == 0) ok = wait_counter_ge(a, scanned_ctr(a), (unsigned long long)tile + 1ull) ? 1 : 0;
+            if (!__shfl_sync(kFull, ok, 0)) return false;
+            Mt = lane < NWT ? __ldcg(a.marks + tile * NWT + lane) : 0u;
+            const int4 rv = __ldcg(reinterpret_cast<const int4 *>(recs + tile));
+            r = TileRec{rv.x, rv.y, rv.z, rv.w};
+            const longlong2 ev = __ldcg(reinterpret_cast<const longlong2 *>(exs + tile));
+            e.m = ev.x;
+            e.s = (int32_t)(ev.y & 0xffffffffll);
+            e.tr = (int32_t)(ev.y >> 32);
+        } else {
+            Mt = lane < NWT ? a.marks[tile * NWT + lane] : 0u;
+            r = recs[tile];
+            e = exs[tile];
+        }
+        return true;
     };
 
     uint32_t phase_bit = 0;
@@ -445,14 +517,15 @@ __global__ void __launch_bounds__(256, 2) daq_compact_kernel(const __grid_consta
     uint32_t nMt = 0;
     TileRec nr{0, 0, 0, 0};
     TileExcl ne{0, 0, 0};
-    if ((long long)blockIdx.x < total) {
-        if (tid == 32) start_load(blockIdx.x);
-        if (warp == 0) load_inputs(blockIdx.x, nMt, nr, ne);
+    int in_ok = 1;
+    if (first < total) {
+        if (tid == 32) start_load(first);
+        if (warp == 0) in_ok = load_inputs(first, nMt, nr, ne) ? 1 : 0;
     }
-    for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        __syncthreads();  // tinfo holds this tile
+    for (long long tile = first; tile < total; tile += G) {
+        if (__syncthreads_or(!in_ok)) break;  // tinfo holds this tile; warp 0 has its inputs
         const TileInfo T = *tinfo;
-        if (!a.use_tma) plain_tile_load_b(a, T, slot, tid, 256);
+        if (!a.use_tma) plain_tile_load_b(a, T, slot, tid, nthr);
         if (warp == 0) {
             const Agg g = words_from_marks<TW>(nMt, (nr.flags >> 1) & 1, (nr.flags >> 2) & 1,
                                                (int)(T.t_end - T.t0), W, nullptr, lane);
@@ -487,13 +560,14 @@ __global__ void __launch_bounds__(256, 2) daq_compact_kernel(const __grid_consta
         const long long gs = ex.m * rb;
         const int phase = (int)(gs & 15);
         const int nt = (int)(T.t_end - T.t0);
-        for (int it = warp; it < (nt + 63) / 64; it += 8) compact_step(a, smem_addr(slot), it, nt, W.m, W.mb, stage,
-                                                                        phase, lane);
+        for (int it = warp; it < (nt + 63) / 64; it += nwarps)
+            compact_step(a, smem_addr(slot), it, nt, W.m, W.mb, stage, phase, lane);
         __syncthreads();  // rows staged; the slot is free
-        const long long next = tile + gridDim.x;
+        if (kFused && tid == 0) atomicAdd(compacted_ctr(a), 1ull);
+        const long long next = tile + G;
         if (next < total) {
             if (tid == 32) start_load(next);
-            if (warp == 0) load_inputs(next, nMt, nr, ne);
+            if (warp == 0) in_ok = load_inputs(next, nMt, nr, ne) ? 1 : 0;
         }
         if (tid == 0) trace_stamp(a, tile, 7);
         // rows [ex.m, ex.m + agg.m) <- stage bytes [phase, phase + agg.m * 2X)
@@ -528,6 +602,103 @@ __global__ void __launch_bounds__(256, 2) daq_compact_kernel(const __grid_consta
         if (tid == 0) trace_stamp(a, tile, 9);
     }
     if (tid == 0 && store_pending) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+template <int TW>
+__global__ void __launch_bounds__(256, 2) daq_compact_kernel(const __grid_constant__ KArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    compact_role<TW, false>(a, smem, blockIdx.x, gridDim.x);
+}
+
+// ============================================================================ single-launch form
+// Scanner: tiles in order, blockDim.x at a time.  Each thread waits for its
+// tile's published record, the block scans the aggregates (carrying the
+// prefix of everything before), writes every tile's exclusive prefix, then
+// releases the scanned counter.
+__device__ __forceinline__ void scan_role(const KArgs &a)
+{
+    __shared__ Agg s_wtot[32];
+    __shared__ Agg s_carry;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const long long total = a.fill_tile_start[a.n_fills];
+    TileExcl *out = reinterpret_cast<TileExcl *>(a.excl);
+    const TileRec *recs = reinterpret_cast<const TileRec *>(a.recs);
+    if (tid == 0) {
+        s_carry = agg_identity();
+        s_fail = 0;
+    }
+    __syncthreads();
+    for (long long base = 0; base < total; base += blockDim.x) {
+        const long long t = base + tid;
+        Agg v = agg_identity();
+        TileRec r{0, 0, 0, 1};
+        if (t < total) {
+            unsigned long long lo = 0, hi = 0;
+            ld_acquire_b128(recs + t, lo, hi);
+            const uint64_t t0 = global_ns();
+            for (uint32_t i = 0; !((hi >> 32) & (unsigned long long)kRecValid); ++i) {
+                __nanosleep(128);
+                ld_acquire_b128(recs + t, lo, hi);
+                if ((i & 63u) == 63u && (aborted(a) || global_ns() - t0 > kWaitLimitNs)) {
+                    s_fail = 1;
+                    break;
+                }
+            }
+            r = TileRec{(int32_t)(lo & 0xffffffffull), (int32_t)(lo >> 32), (int32_t)(hi & 0xffffffffull),
+                        (int32_t)(hi >> 32)};
+            v = rec_agg(r);
+        }
+        // inclusive scan of v across the block
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const Agg o = shfl_up_agg(v, d);
+            if (lane >= d) v = combine(o, v);
+        }
+        if (lane == 31) s_wtot[warp] = v;
+        __syncthreads();
+        if (s_fail) {
+            if (tid == 0) set_status_bit(a, DAQ_DEV_TIMEOUT);
+            return;
+        }
+        Agg pre = s_carry;
+        for (int w = 0; w < warp; ++w) pre = combine(pre, s_wtot[w]);
+        const Agg incl = combine(pre, v);
+        const Agg vprev = shfl_up_agg(v, 1);  // warp-inclusive value of the previous lane
+        if (t < total) {
+            const Agg ex = lane == 0 ? pre : combine(pre, vprev);
+            TileExcl e;
+            e.m = ex.m;
+            e.s = (int32_t)ex.s;
+            e.tr = (int32_t)ex.tr;
+            out[t] = e;
+            if (t == total - 1) write_counts(a, t, incl);
+            __threadfence();
+        }
+        __syncthreads();
+        if (tid == 0) {
+            Agg c = s_carry;
+            for (int w = 0; w < nw; ++w) c = combine(c, s_wtot[w]);
+            s_carry = c;
+            __threadfence();
+            const long long done = base + blockDim.x < total ? base + blockDim.x : total;
+            st_release_u64(scanned_ctr(a), (unsigned long long)done);
+        }
+        __syncthreads();
+    }
+}
+
+// Roles by block: 0 scanner, [1, G/2) compact, [G/2, G) count.  Launched
+// cooperatively, so every CTA is resident and the waits between roles end.
+template <int TW>
+__global__ void __launch_bounds__(kCountThreads, 2) daq_fused_kernel(const __grid_constant__ KArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const long long G = gridDim.x, half = G / 2;
+    if (blockIdx.x == 0) scan_role(a);
+    else if (blockIdx.x < half) compact_role<TW, true>(a, smem, blockIdx.x - 1, half - 1);
+    else count_role<TW, true>(a, smem, blockIdx.x - half, G - half);
 }
 
 }  // namespace daq

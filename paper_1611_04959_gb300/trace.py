@@ -65,20 +65,22 @@ def main():
     ap.add_argument("--grid", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--flags", type=int, default=0, help="daq_params.flags (1 = skip Q, 2 = skip islands)")
+    ap.add_argument("--lag", type=int, default=0, help="daq_params.lag_tiles (single-launch form, grid -4)")
     ap.add_argument("--out", default=None, help="save the raw trace (.npy)")
     args = ap.parse_args()
     w = W.scaled(W.PLAIN_FULL_FILL, n_calo=args.calos)
     s = torch.from_numpy(synth.generate(w.config())).cuda()
     F, C, X, N = s.shape
-    p = daq.make_params(**w.params(), tile=args.tile, grid=args.grid)
+    p = daq.make_params(**w.params(), tile=args.tile, grid=args.grid, lag_tiles=args.lag)
     n_tiles = daq.daq_trace_tiles(C, X, N, F, p)
     trace = torch.zeros((n_tiles, DAQ_TRACE_WORDS), dtype=torch.int64, device="cuda")
-    res = daq.process_fills(s, tile=args.tile, grid=args.grid, flags=args.flags, **w.params())   # warm-up
+    res = daq.process_fills(s, tile=args.tile, grid=args.grid, flags=args.flags, lag_tiles=args.lag,
+                            **w.params())   # warm-up
     outs, ws = res["outputs"], res["workspace"]
     for _ in range(3):
         daq.process_fills(s, tile=args.tile, grid=args.grid, outputs=outs, workspace=ws, flags=args.flags,
-                          **w.params())
-    p = daq.make_params(**w.params(), tile=args.tile, grid=args.grid, flags=args.flags,
+                          lag_tiles=args.lag, **w.params())
+    p = daq.make_params(**w.params(), tile=args.tile, grid=args.grid, flags=args.flags, lag_tiles=args.lag,
                         stream=torch.cuda.current_stream())
     p.workspace, p.workspace_bytes = ws.data_ptr(), ws.numel()
     p.trace = trace.data_ptr()
