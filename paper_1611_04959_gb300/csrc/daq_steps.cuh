@@ -217,6 +217,12 @@ __device__ __forceinline__ void issue_tile_load(const KArgs &a, const TileInfo &
 {
     const int c0 = (int)(T.t0 - a.hl);
     const int c1 = (int)(((long long)T.f * a.n_calo + T.c) * a.n_xtal);
+    if (a.mode == kModeFused) {  // the compact role re-reads these lines soon: keep them in L2
+        const uint64_t pol = l2_policy_evict_last();
+        for (int k = 0; k < a.nbox; ++k)
+            tma_load_2d_hint(slot + (size_t)k * a.box_stride, &a.tmap, c0 + k * a.boxw, c1, bar, pol);
+        return;
+    }
     for (int k = 0; k < a.nbox; ++k) tma_load_2d(slot + (size_t)k * a.box_stride, &a.tmap, c0 + k * a.boxw, c1, bar);
 }
 
@@ -457,6 +463,30 @@ __device__ __forceinline__ Agg words_from_marks(uint32_t Mt, uint32_t m_prev, ui
     Agg agg;
     agg.m = tot & 0xffffu;
     agg.s = tot >> 16;
+    agg.tr = nt - 1 - lz;
+    agg.full = (lz < 0) && m_prev;
+    agg.poison = 0;
+    return agg;
+}
+
+// The tile's aggregate alone (the count pass needs no per-word prefixes): the
+// same totals as words_from_marks - marked samples, island starts, trailing
+// run - from three warp reductions.
+template <int TW>
+__device__ __forceinline__ Agg agg_from_marks(uint32_t Mt, uint32_t m_prev, int nt, int lane)
+{
+    constexpr int NWT = TW / 32;
+    if (lane >= NWT) Mt = 0u;
+    uint32_t below = __shfl_up_sync(kFull, Mt, 1);
+    if (lane == 0) below = m_prev << 31;
+    const uint32_t St = Mt & ~((Mt << 1) | (below >> 31));
+    const unsigned m = __reduce_add_sync(kFull, (unsigned)__popc(Mt));
+    const unsigned st = __reduce_add_sync(kFull, (unsigned)__popc(St));
+    const uint32_t zeros = ~Mt & range_mask(32ll * lane, 0, nt);
+    const int lz = (int)__reduce_max_sync(kFull, zeros ? (unsigned)(32 * lane + 32 - __clz(zeros)) : 0u) - 1;
+    Agg agg;
+    agg.m = m;
+    agg.s = st;
     agg.tr = nt - 1 - lz;
     agg.full = (lz < 0) && m_prev;
     agg.poison = 0;

@@ -26,7 +26,7 @@
 namespace daq {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanPer = 16;  // tiles per scan thread
+constexpr int kScanPer = 4;  // tiles per scan thread
 constexpr int kScanChunk = kScanThreads * kScanPer;
 
 struct __align__(16) TileRec {
@@ -44,6 +44,12 @@ __device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t by
 {
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
                  "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_s2g_hint(void *dst, const void *src, uint32_t bytes, uint64_t policy)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(dst),
+                 "r"(smem_addr(src)), "r"(bytes), "l"(policy)
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
@@ -249,9 +255,7 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
             const TileInfo T = tinfo_m[s];
             unsigned edges;
             const uint32_t Mt = tile_marks<TW>(a, T, abyte0 + 128 * s, &edges, lane);
-            const Agg agg = words_from_marks<TW>(Mt, edges & 1u, edges >> 1, (int)(T.t_end - T.t0),
-                                                 TileWords{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
-                                                 nullptr, lane);
+            const Agg agg = agg_from_marks<TW>(Mt, edges & 1u, (int)(T.t_end - T.t0), lane);
             if (lane < NWT) a.marks[T.tile * NWT + lane] = Mt;
             if (kFused) {
                 __threadfence();
@@ -349,10 +353,16 @@ __global__ void __launch_bounds__(kScanThreads) daq_scan_apply_kernel(const __gr
     const long long total = a.fill_tile_start[a.n_fills];
     const long long chunk0 = (long long)blockIdx.x * kScanChunk;
     if (chunk0 >= total) return;
-    if (threadIdx.x == 0) {
+    {   // prefix of the earlier blocks: each thread combines a contiguous run of
+        // block aggregates, then an ordered block scan joins the runs
+        const unsigned nb = blockIdx.x, per = (nb + kScanThreads - 1) / kScanThreads;
+        const unsigned lo = threadIdx.x * per, hi = min(nb, lo + per);
         Agg p = agg_identity();
-        for (unsigned b = 0; b < blockIdx.x; ++b) p = combine(p, a.blockagg[b]);
-        s_prefix = p;
+        for (unsigned b = lo; b < hi; ++b) p = combine(p, a.blockagg[b]);
+        Agg all;
+        block_scan_incl(p, warp_tot, &all);
+        if (threadIdx.x == 0) s_prefix = all;
+        __syncthreads();
     }
     const long long base = chunk0 + (long long)threadIdx.x * kScanPer;
     const TileRec *recs = reinterpret_cast<const TileRec *>(a.recs);
@@ -424,6 +434,12 @@ __device__ __forceinline__ void issue_tile_load_b(const KArgs &a, const TileInfo
 {
     const int c0 = (int)T.t0;
     const int c1 = (int)(((long long)T.f * a.n_calo + T.c) * a.n_xtal);
+    if (a.mode == kModeFused) {  // last use of these lines
+        const uint64_t pol = l2_policy_evict_first();
+        for (int k = 0; k < a.nbox_b; ++k)
+            tma_load_2d_hint(slot + (size_t)k * a.box_stride_b, &a.tmap_b, c0 + k * a.boxw_b, c1, bar, pol);
+        return;
+    }
     for (int k = 0; k < a.nbox_b; ++k)
         tma_load_2d(slot + (size_t)k * a.box_stride_b, &a.tmap_b, c0 + k * a.boxw_b, c1, bar);
 }
@@ -585,7 +601,10 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
             // stage offset of global byte x is phase + (x - gs); a16 maps to a multiple of 16
             if (tid == 0 && b16 > a16) {
                 fence_proxy_async_smem();
-                bulk_s2g(g + a16, stage + phase + (a16 - gs), (uint32_t)(b16 - a16));
+                if (kFused)  // pool rows are not read again here: let them leave L2 first
+                    bulk_s2g_hint(g + a16, stage + phase + (a16 - gs), (uint32_t)(b16 - a16), l2_policy_evict_first());
+                else
+                    bulk_s2g(g + a16, stage + phase + (a16 - gs), (uint32_t)(b16 - a16));
                 bulk_commit();
                 store_pending = true;
             }
