@@ -180,6 +180,7 @@ def bench_gb300(args, ws, rank, local):
     import synth
     import paper_1611_04959_gb300 as daq
     from paper_1611_04959_gb300 import build as daq_build
+    from paper_1611_04959_gb300 import replicas
     from synth import workloads as W
 
     daq_build.build()
@@ -193,7 +194,9 @@ def bench_gb300(args, ws, rank, local):
     params = w.params()
     F, C, X, N = w.n_fills, w.n_calo, 54, w.n_samples
     host = torch.empty((F, C, X, N), dtype=torch.int16).pin_memory()
-    synth.generate(w.config(), out=host.numpy(), n_threads=os.cpu_count() or 1)
+    # rank r processes fill r of the generator (its own share; weak scaling)
+    synth.generate(W.scaled(w, n_fills=max(1, ws)).config(), out=host.numpy(), n_threads=os.cpu_count() or 1,
+                   fills=(rank, 1))
     samples = host.to(dev)
     raw_bytes = samples.numel() * 2
 
@@ -220,11 +223,8 @@ def bench_gb300(args, ws, rank, local):
 
     def barrier():
         torch.cuda.synchronize(dev)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.zeros(1, device=dev)
-            dist.all_reduce(t)
-            torch.cuda.synchronize(dev)
+        replicas.barrier(dev)
+        torch.cuda.synchronize(dev)
 
     # ---- warm-up
     with torch.cuda.stream(stream):
@@ -258,12 +258,7 @@ def bench_gb300(args, ws, rank, local):
     count_ms = [e[1].elapsed_time(e[2]) for e in evs]
     scan_ms = [e[2].elapsed_time(e[3]) for e in evs]
     compact_ms = [e[3].elapsed_time(e[4]) for e in evs]
-    t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
-    value = K * raw_bytes * ws / (elapsed_ms * 1e-3) / 1e9
+    _, elapsed_ms, value = replicas.aggregate(K * raw_bytes, elapsed_ms, dev)
 
     # ---- roofline of the dominant kernel: the compact pass (reads the samples, writes the islands)
     peak, peak_kind = measured_peaks()
@@ -359,16 +354,12 @@ def bench_gb300(args, ws, rank, local):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ems = e0.elapsed_time(e1)
-        te = torch.tensor([ems], device=dev, dtype=torch.float64)
-        if ws > 1:
-            import torch.distributed as dist
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        ems = float(te.item())
+        _, ems, e2e_value = replicas.aggregate(Ke * raw_bytes, ems, dev)
         d2h = 32 + int(counts_h[0]) * 24 + int(counts_h[1]) * X * 2
         bw = copy_bandwidth(torch, dev, host, samples, pool_h, out.pool, int(counts_h[1]))
         e2e_bound = raw_bytes / max(raw_bytes / bw["h2d_gbs"], d2h / bw["d2h_gbs"],
                                     (raw_bytes + d2h) / bw["bidir_gbs"]) if bw["h2d_gbs"] else None
-        result["e2e"] = {"value": round(Ke * raw_bytes * ws / (ems * 1e-3) / 1e9, 2), "unit": UNIT,
+        result["e2e"] = {"value": round(e2e_value, 2), "unit": UNIT,
                          "h2d_bytes_per_step": raw_bytes, "d2h_bytes_per_step": d2h, "steps": Ke,
                          "ms_per_step": round(ems / Ke, 3),
                          "api": "daq_process_fills_host (pinned host buffers; copy-in, processing and copy-out "
