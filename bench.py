@@ -316,6 +316,14 @@ def bench_gb300(args, ws, rank, local):
     if not args.no_sparse and not args.quick:
         result["sparse"] = bench_sparse(args, torch, dev, daq, synth, W)
 
+    # ---- island-finding efficiency across thresholds (Fig. 2)
+    if not args.no_threshold_scan and not args.quick and rank == 0:
+        scan = threshold_scan(torch, dev, daq, synth, W)
+        result["threshold_scan"] = {"datasets": scan["datasets"],
+                                    "slope": {t: v["slope"] for t, v in scan["thresholds"].items()},
+                                    "corr": {t: v["corr"] for t, v in scan["thresholds"].items()},
+                                    "ratio_of_totals": {t: v["ratio_of_totals"] for t, v in scan["thresholds"].items()}}
+
     # ---- plain form: one CTA per tile, no persistence
     if not args.quick:
         pp, _ = make_p(grid=-1)
@@ -603,6 +611,49 @@ def bench_stress(args, torch, dev, daq, synth, W) -> dict:
     return res
 
 
+THRESHOLDS = (5, 10, 15, 20, 30, 50, 100, 300, 1000)
+
+
+def threshold_scan(torch, dev, daq, synth, W, n_fills: int = 12, n_calo: int = 2, thresholds=THRESHOLDS) -> dict:
+    """Island-finding efficiency across thresholds (the check of Fig. 2):
+    datasets are calorimeter-fills of the sparse regime with pulse rates x
+    log-uniform[0.2, 5]; for each threshold T, the islands the path finds in a
+    dataset are compared with its truth islands - those the same path finds in
+    the dataset's noise-free twin (the same pulses; the generator draws pulses
+    and noise from independent streams).  Reports, per T, the least-squares
+    slope of identified on truth through the origin, the ratio of totals and
+    the correlation over datasets."""
+    import numpy as np
+    w = W.scaled(W.SPARSE_FULL_FILL, n_fills=n_fills, n_calo=n_calo)
+    w0 = W.scaled(W.SPARSE_FULL_FILL, n_fills=n_fills, n_calo=n_calo, noise_sigma=0.0)
+    N = w.n_samples
+    _, rates = synth.fill_plan(w.synth["seed"] + 29, n_fills, N, N, 0.2, 5.0)
+    x = torch.from_numpy(synth.generate(w.config(), rate=rates, n_threads=os.cpu_count() or 1)).to(dev)
+    x0 = torch.from_numpy(synth.generate(w0.config(), rate=rates, n_threads=os.cpu_count() or 1)).to(dev)
+    n_sets = n_fills * n_calo
+    pulses = [len(synth.pulses(w.config(), f, c, N, float(rates[f]))) for f in range(n_fills) for c in range(n_calo)]
+    base = w.params()
+    rows = {}
+    for T in thresholds:
+        per = []
+        for xx in (x, x0):
+            res = daq.process_fills(xx, **dict(base, threshold=int(T)))
+            isl = res["outputs"].islands_host(res["n_islands"])
+            per.append(np.bincount(isl["fill"].astype(np.int64) * n_calo + isl["calo"], minlength=n_sets))
+        ident, truth = per
+        t, i = truth.astype(np.float64), ident.astype(np.float64)
+        slope = float((t * i).sum() / max(1e-9, (t * t).sum()))
+        corr = float(np.corrcoef(t, i)[0, 1]) if t.std() > 0 and i.std() > 0 else None
+        rows[str(T)] = {"slope": round(slope, 4), "ratio_of_totals": round(float(i.sum() / max(1.0, t.sum())), 4),
+                        "corr": None if corr is None else round(corr, 4),
+                        "truth": truth.tolist(), "identified": ident.tolist()}
+    del x, x0
+    torch.cuda.empty_cache()
+    return {"datasets": f"{n_sets} calorimeter-fills (sparse regime: sum noise sigma ~3 ADC; pulse rate x "
+                        "log-uniform[0.2, 5] per fill); truth = islands of the noise-free twin at the same threshold",
+            "pre": base["pre"], "post": base["post"], "injected_pulses": pulses, "thresholds": rows}
+
+
 def burst_schedule(n_fills: int, speed: float, t0_us: float) -> list:
     """Arrival times (us) of the accelerator cycle replayed `speed` times
     faster: bursts of 8 fills 10 ms apart, two bursts per 1.4 s cycle (the
@@ -749,6 +800,7 @@ def main():
     ap.add_argument("--no-stress", action="store_true", help="skip the 48-fill (69.67 GB) stress batch")
     ap.add_argument("--stress-steps", type=int, default=10)
     ap.add_argument("--no-sparse", action="store_true", help="skip the sparse-regime fill")
+    ap.add_argument("--no-threshold-scan", action="store_true", help="skip the island-efficiency threshold scan")
     ap.add_argument("--sparse-steps", type=int, default=1000)
     ap.add_argument("--serve-pool", type=int, default=4, help="distinct device fills the served stream cycles over")
     ap.add_argument("--serve-fills", type=int, default=1024, help="fills per served run at 10x and 100x")

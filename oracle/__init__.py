@@ -53,6 +53,9 @@ def _bind(path: str):
     lib.oracle_process_fills.argtypes = [vp, i32, i32, i32, i64, vp, ctypes.POINTER(OracleParams), vp,
                                          i64, vp, i64, vp, vp, vp, i32]
     lib.oracle_process_fills.restype = ctypes.c_int
+    if hasattr(lib, "oracle_crystal_sum"):
+        lib.oracle_crystal_sum.argtypes = [vp, i32, i32, i32, i64, vp, i32, vp]
+        lib.oracle_crystal_sum.restype = ctypes.c_int
     return lib
 
 
@@ -144,6 +147,23 @@ class Oracle:
                     n_islands=n_isl, n_rows=n_rows)
 
 
+    def crystal_sum(self, samples: np.ndarray, fill_len=None, ped_samples: int = 100,
+                    q: np.ndarray | None = None) -> np.ndarray:
+        """Per-crystal full-resolution fill sum of samples[F][C][X][pitch]:
+        q[c][x][t] (int64) += s - pedestal over every fill, t < the fill's length."""
+        samples = np.ascontiguousarray(samples, dtype=np.int16)
+        F, C, X, N = samples.shape
+        if q is None:
+            q = np.zeros((C, X, N), np.int64)
+        assert q.dtype == np.int64 and q.flags.c_contiguous and q.shape == (C, X, N)
+        lens = None if fill_len is None else np.ascontiguousarray(fill_len, dtype=np.int32)
+        rc = self._lib.oracle_crystal_sum(samples.ctypes.data, F, C, X, N, _ptr(lens), int(ped_samples),
+                                          q.ctypes.data)
+        if rc != 0:
+            raise ValueError("oracle rejected the arguments")
+        return q
+
+
 _default = None
 
 
@@ -164,3 +184,7 @@ def calofill(*a, **k) -> dict:
 
 def process_fills(*a, **k) -> dict:
     return _oracle().process_fills(*a, **k)
+
+
+def crystal_sum(*a, **k) -> np.ndarray:
+    return _oracle().crystal_sum(*a, **k)

@@ -25,6 +25,11 @@
  *
  * Step 4 is written as an explicit scan of every window (O(len * (pre+post))),
  * deliberately not the GPU's bit-parallel form.
+ *
+ * Per-crystal full-resolution fill sum (the form Table 2's fill-by-fill sum
+ * kernel suggests with one thread per crystal and sample, 54 x 560,000):
+ *   Qx[c][x][t] += s[f][c][x][t] - P[f][c][x]   for t < len_f, over all fills f
+ *   (pedestal P as in step 1; int64 accumulators).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -234,5 +239,29 @@ int oracle_process_fills(const int16_t *samples, int32_t n_fills, int32_t n_calo
     free(cf_nisl);
     free(cf_rows);
     free(cf_len);
+    return 0;
+}
+
+/*
+ * Per-crystal full-resolution fill sum: for every fill f, calorimeter c,
+ * crystal x and sample t < len_f, add s[f][c][x][t] - P[f][c][x] to
+ * q[c][x][t] (int64, layout [n_calo][n_xtal][pitch]; samples past a fill's
+ * length add nothing).  fill_len may be NULL (every fill is pitch long).
+ */
+int oracle_crystal_sum(const int16_t *samples, int32_t n_fills, int32_t n_calo, int32_t n_xtal, int64_t pitch,
+                       const int32_t *fill_len, int32_t ped_samples, int64_t *q)
+{
+    if (n_fills < 0 || n_calo < 0 || n_xtal < 1 || pitch < 0 || ped_samples < 1 || (!q && n_calo > 0)) return -1;
+    for (int32_t f = 0; f < n_fills; ++f) {
+        int64_t len = fill_len ? fill_len[f] : pitch;
+        if (len < 0 || len > pitch) return -1;
+        for (int32_t c = 0; c < n_calo; ++c)
+            for (int32_t x = 0; x < n_xtal; ++x) {
+                const int16_t *row = samples + (((int64_t)f * n_calo + c) * n_xtal + x) * pitch;
+                const int64_t ped = oracle_pedestal(row, len, ped_samples);
+                int64_t *qrow = q + ((int64_t)c * n_xtal + x) * pitch;
+                for (int64_t t = 0; t < len; ++t) qrow[t] += (int64_t)row[t] - ped;
+            }
+    }
     return 0;
 }

@@ -66,6 +66,8 @@ def pin_golden(orc):
     assert files, "golden fixtures missing"
     for fn in files:
         g = json.load(open(fn))
+        if g.get("kind", "islands") != "islands":
+            continue
         s = np.array(g["samples"], dtype=np.int16)
         r = orc.calofill(s, g["params"], length=g["length"])
         e = g["expect"]
@@ -205,8 +207,42 @@ def pin_fill_sum_accumulates(orc):
     assert np.array_equal(res["q"], np.concatenate([q[0].ravel(), q[1].ravel()]))
 
 
+def pin_crystal_sum_golden(orc):
+    """Per-crystal full-resolution fill sum on the hand-derived fixture."""
+    n = 0
+    for fn in sorted(glob.glob(os.path.join(GOLDEN, "*.json"))):
+        g = json.load(open(fn))
+        if g.get("kind") != "crystal_sum":
+            continue
+        q = orc.crystal_sum(np.array(g["samples"], np.int16), fill_len=g["fill_len"], ped_samples=g["ped_samples"])
+        assert q.tolist() == g["expected_q"], os.path.basename(fn)
+        n += 1
+    assert n >= 1, "crystal-sum fixture missing"
+
+
+def pin_crystal_sum_matches_decimated_q(orc):
+    """Summed over crystals and over the samples of a bin, the per-crystal fill
+    sum is the decimated fill sum Q_D (the oracle's separate Q-method path)."""
+    rng = np.random.default_rng(8)
+    F, C, X, N = 3, 3, 4, 61
+    s = rng.integers(-40, 400, size=(F, C, X, N)).astype(np.int16)
+    lens = np.array([61, 29, 4], np.int32)
+    params = dict(threshold=10_000, pre=1, post=1, ped_samples=5, decim=(4, 7))
+    qx = orc.crystal_sum(s, fill_len=lens, ped_samples=5)
+    qd = orc.process_fills(s, params, fill_len=lens)["q"]
+    off = 0
+    for D in (4, 7):
+        nb = math.ceil(N / D)
+        want = qd[off: off + C * nb].reshape(C, nb)
+        off += C * nb
+        per_t = qx.sum(axis=1)                      # [C][N]
+        got = np.stack([per_t[:, k * D: k * D + D].sum(axis=1) for k in range(nb)], axis=1)
+        assert np.array_equal(got, want), D
+
+
 PINS = [pin_golden, pin_single_crossing, pin_merge_boundary, pin_threshold_strict_and_extremes,
-        pin_pedestal_rounding, pin_decimation, pin_against_brute, pin_fill_sum_accumulates]
+        pin_pedestal_rounding, pin_decimation, pin_against_brute, pin_fill_sum_accumulates,
+        pin_crystal_sum_golden, pin_crystal_sum_matches_decimated_q]
 
 
 # ---------------------------------------------------------------- invariants on any output

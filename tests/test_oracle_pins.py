@@ -148,6 +148,10 @@ MUTANTS = {
     "crystal_dropped": ("for (int32_t x = 0; x < n_xtal; ++x) acc += s[(int64_t)x * pitch + t];",
                         "for (int32_t x = 1; x < n_xtal; ++x) acc += s[(int64_t)x * pitch + t];"),
     "pool_row_offset_lost": ("isl[tot_isl].pool_row += tot_rows;", "isl[tot_isl].pool_row += 0;"),
+    "xtal_sum_pedestal_dropped": ("qrow[t] += (int64_t)row[t] - ped;", "qrow[t] += (int64_t)row[t];"),
+    "xtal_sum_ignores_fill_len": ("for (int64_t t = 0; t < len; ++t) qrow[t]", "for (int64_t t = 0; t < pitch; ++t) qrow[t]"),
+    "xtal_sum_rows_transposed": ("int64_t *qrow = q + ((int64_t)c * n_xtal + x) * pitch;",
+                                 "int64_t *qrow = q + ((int64_t)x * n_calo + c) * pitch;"),
 }
 
 
