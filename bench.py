@@ -316,6 +316,10 @@ def bench_gb300(args, ws, rank, local):
     if not args.no_sparse and not args.quick:
         result["sparse"] = bench_sparse(args, torch, dev, daq, synth, W)
 
+    # ---- per-crystal full-resolution fill sum
+    if not args.no_crystal_sum and not args.quick:
+        result["crystal_sum"] = bench_crystal_sum(args, torch, dev, daq, samples)
+
     # ---- island-finding efficiency across thresholds (Fig. 2)
     if not args.no_threshold_scan and not args.quick and rank == 0:
         scan = threshold_scan(torch, dev, daq, synth, W)
@@ -611,6 +615,41 @@ def bench_stress(args, torch, dev, daq, synth, W) -> dict:
     return res
 
 
+def bench_crystal_sum(args, torch, dev, daq, samples) -> dict:
+    """Per-crystal full-resolution fill sum on the full fill: int64 Q of
+    24 x 54 x 560,000 bins resident on the device, one call per fill."""
+    F, C, X, N = (int(v) for v in samples.shape)
+    q = torch.zeros((C, X, N), dtype=torch.int64, device=dev)
+    stream = torch.cuda.Stream(dev)
+    p = daq.make_params(stream=stream)
+    need = daq.daq_crystal_sum_workspace_size(C, X, F)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    p.workspace, p.workspace_bytes = ws.data_ptr(), need
+    for _ in range(3):
+        assert daq.daq_crystal_sum(samples.data_ptr(), C, X, N, F, p, q.data_ptr()) == daq.DAQ_OK
+    K = max(3, min(args.steps, args.crystal_steps))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(K):
+        daq.daq_crystal_sum(samples.data_ptr(), C, X, N, F, p, q.data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / K
+    raw = F * C * X * N * 2
+    alg = raw + C * X * N * 16
+    peak = measured_peaks()[0]
+    del q, ws
+    torch.cuda.empty_cache()
+    return {"value": round(raw / (ms * 1e-3) / 1e9, 2), "unit": UNIT, "steps": K, "ms_per_fill": round(ms, 4),
+            "workload": "full fill 24 x 54 x 560,000 int16 into int64 Q[24][54][560,000] (5.8 GB, device-resident)",
+            "roofline": {"bound": "hbm", "achieved": round(alg / (ms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4),
+                         "algorithmic_bytes_per_launch": alg,
+                         "note": "2 B per sample read + 16 B per crystal-sample of Q read and written"},
+            "gpu_launches": 2 * K}
+
+
 THRESHOLDS = (5, 10, 15, 20, 30, 50, 100, 300, 1000)
 
 
@@ -801,6 +840,8 @@ def main():
     ap.add_argument("--stress-steps", type=int, default=10)
     ap.add_argument("--no-sparse", action="store_true", help="skip the sparse-regime fill")
     ap.add_argument("--no-threshold-scan", action="store_true", help="skip the island-efficiency threshold scan")
+    ap.add_argument("--no-crystal-sum", action="store_true", help="skip the per-crystal full-resolution fill sum")
+    ap.add_argument("--crystal-steps", type=int, default=50)
     ap.add_argument("--sparse-steps", type=int, default=1000)
     ap.add_argument("--serve-pool", type=int, default=4, help="distinct device fills the served stream cycles over")
     ap.add_argument("--serve-fills", type=int, default=1024, help="fills per served run at 10x and 100x")

@@ -487,6 +487,29 @@ int daq_server_destroy(daq_server *s);
 /* Summarise records (any order): latency percentiles, deadtime, throughput. */
 int daq_serving_summarize(const daq_fill_record *recs, int64_t n, daq_serving_summary *out);
 
+/*
+ * Per-crystal full-resolution fill sum (Table 2, fill-by-fill sum kernel in
+ * the per-crystal, per-sample form its 30-million-thread count suggests).
+ * For every fill f of the call, calorimeter c, crystal x and sample t < len_f:
+ *     q_xtal[c][x][t] += samples[f][c][x][t] - P[f][c][x]
+ * with P the crystal's pedestal as in daq_params.ped_samples (rounded half up).
+ *   samples   device int16[n_fills][n_calo][n_xtal][n_samples].
+ *   q_xtal    device int64[n_calo][n_xtal][n_samples], 16-byte aligned,
+ *             accumulated (resident across calls); samples past a fill's
+ *             length add nothing.
+ *   params    ped_samples, fill_len (device, nullable; out-of-range lengths are
+ *             clamped and flagged), stream, flags (DAQ_SYNC: wait and return
+ *             DAQ_EINVAL if a fill length was out of range), workspace of at
+ *             least daq_crystal_sum_workspace_size() bytes (16-byte aligned).
+ *             Other fields are ignored.
+ * Integer-exact; HBM traffic is the samples once plus q_xtal read and written
+ * once per call (16 bytes per crystal-sample), so batching fills in one call
+ * divides the Q traffic among them.
+ */
+int daq_crystal_sum_workspace_size(int n_calo, int n_xtal, int n_fills, size_t *bytes);
+int daq_crystal_sum(const int16_t *samples, int n_calo, int n_xtal, int64_t n_samples, int n_fills,
+                    const daq_params *params, int64_t *q_xtal);
+
 /* Upper bound on the tiles of a call with these sizes and parameters (rows of
  * the trace buffer); 0 on invalid arguments. */
 int64_t daq_trace_tiles(int n_calo, int n_xtal, int64_t n_samples, int n_fills, const daq_params *params);

@@ -145,6 +145,10 @@ def lib():
             L.daq_batch_plan_destroy.restype = i32
             L.daq_tune_cache_clear.argtypes = []
             L.daq_tune_cache_clear.restype = None
+            L.daq_crystal_sum_workspace_size.argtypes = [i32, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
+            L.daq_crystal_sum_workspace_size.restype = i32
+            L.daq_crystal_sum.argtypes = [vp, i32, i32, i64, i32, ctypes.POINTER(DaqParams), vp]
+            L.daq_crystal_sum.restype = i32
             L.daq_server_create.argtypes = [ctypes.POINTER(DaqServerConfig), ctypes.POINTER(vp)]
             L.daq_server_create.restype = i32
             L.daq_server_submit.argtypes = [vp, vp, i32, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(i64)]
@@ -254,6 +258,44 @@ def daq_batch_plan_destroy(plan) -> int:
 
 def daq_tune_cache_clear() -> None:
     lib().daq_tune_cache_clear()
+
+
+def daq_crystal_sum_workspace_size(n_calo: int, n_xtal: int, n_fills: int) -> int:
+    out = ctypes.c_size_t(0)
+    rc = lib().daq_crystal_sum_workspace_size(n_calo, n_xtal, n_fills, ctypes.byref(out))
+    if rc:
+        raise DaqError(rc, "daq_crystal_sum_workspace_size")
+    return int(out.value)
+
+
+def daq_crystal_sum(samples_ptr: int, n_calo: int, n_xtal: int, n_samples: int, n_fills: int, params: DaqParams,
+                    q_ptr: int | None) -> int:
+    return int(lib().daq_crystal_sum(samples_ptr, n_calo, n_xtal, n_samples, n_fills, ctypes.byref(params), q_ptr))
+
+
+def crystal_sum(samples, q=None, ped_samples: int = 100, fill_len=None, stream=None, sync: bool = True,
+                workspace=None):
+    """Per-crystal full-resolution fill sum of a CUDA int16 tensor [F][C][X][N]
+    into q (int64 [C][X][N], allocated zeroed if not given).  Returns q."""
+    import torch
+    if not samples.is_cuda or samples.dtype != torch.int16 or samples.dim() != 4 or not samples.is_contiguous():
+        raise ValueError("samples must be a contiguous CUDA int16 tensor [fills][calo][xtal][samples]")
+    F, C, X, N = (int(v) for v in samples.shape)
+    dev = samples.device
+    if q is None:
+        q = torch.zeros((C, X, N), dtype=torch.int64, device=dev)
+    if fill_len is not None and not torch.is_tensor(fill_len):
+        fill_len = torch.as_tensor(np.asarray(fill_len, np.int32), device=dev)
+    stream = torch.cuda.current_stream(dev) if stream is None else stream
+    p = make_params(ped_samples=ped_samples, fill_len=fill_len, stream=stream, flags=DAQ_SYNC if sync else 0)
+    need = daq_crystal_sum_workspace_size(C, X, F)
+    if workspace is None or workspace.numel() * workspace.element_size() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    p.workspace, p.workspace_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    rc = daq_crystal_sum(samples.data_ptr(), C, X, N, F, p, q.data_ptr())
+    if rc != DAQ_OK:
+        raise DaqError(rc, "daq_crystal_sum")
+    return q
 
 
 def daq_status_from_counts(counts_host) -> int:
