@@ -53,6 +53,11 @@ def _bind(path: str):
     lib.oracle_process_fills.argtypes = [vp, i32, i32, i32, i64, vp, ctypes.POINTER(OracleParams), vp,
                                          i64, vp, i64, vp, vp, vp, i32]
     lib.oracle_process_fills.restype = ctypes.c_int
+    if hasattr(lib, "oracle_pack"):
+        lib.oracle_pack.argtypes = [vp, i64, i32, vp, i64]
+        lib.oracle_pack.restype = i64
+        lib.oracle_unpack.argtypes = [vp, i64, vp, i64, i32]
+        lib.oracle_unpack.restype = ctypes.c_int
     if hasattr(lib, "oracle_crystal_sum"):
         lib.oracle_crystal_sum.argtypes = [vp, i32, i32, i32, i64, vp, i32, vp]
         lib.oracle_crystal_sum.restype = ctypes.c_int
@@ -164,6 +169,25 @@ class Oracle:
         return q
 
 
+    def pack(self, pool: np.ndarray) -> np.ndarray:
+        """Packed stream (uint8) of pool rows [rows][n_xtal] int16."""
+        pool = np.ascontiguousarray(pool, dtype=np.int16)
+        rows, X = pool.shape
+        n = int(self._lib.oracle_pack(pool.ctypes.data, rows, X, None, 0))
+        if n < 0:
+            raise ValueError("oracle rejected the arguments")
+        out = np.zeros(n, np.uint8)
+        self._lib.oracle_pack(pool.ctypes.data, rows, X, out.ctypes.data, n)
+        return out
+
+    def unpack(self, stream: np.ndarray, rows: int, n_xtal: int) -> np.ndarray:
+        stream = np.ascontiguousarray(stream, dtype=np.uint8)
+        out = np.zeros((rows, n_xtal), np.int16)
+        if self._lib.oracle_unpack(stream.ctypes.data, stream.size, out.ctypes.data, rows, n_xtal) != 0:
+            raise ValueError("malformed packed stream")
+        return out
+
+
 _default = None
 
 
@@ -188,3 +212,11 @@ def process_fills(*a, **k) -> dict:
 
 def crystal_sum(*a, **k) -> np.ndarray:
     return _oracle().crystal_sum(*a, **k)
+
+
+def pack(*a, **k) -> np.ndarray:
+    return _oracle().pack(*a, **k)
+
+
+def unpack(*a, **k) -> np.ndarray:
+    return _oracle().unpack(*a, **k)

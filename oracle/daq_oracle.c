@@ -26,6 +26,19 @@
  * Step 4 is written as an explicit scan of every window (O(len * (pre+post))),
  * deliberately not the GPU's bit-parallel form.
  *
+ * Packed pool stream (lossless; Sec. 2 has the frontend compress island data
+ * losslessly before event building, without naming the method - this format
+ * is this project's reading):
+ *   header   u32 magic 0x50514144, u32 n_xtal, u64 rows
+ *   offsets  u64[n_blocks + 1], n_blocks = ceil(rows / 32): byte offset of each
+ *            block's payload from the payload start (the last one = its size)
+ *   payload  block b = rows [32b, 32b + 32), the last block padded with copies
+ *            of the final row; for each crystal x, with v_i the sample of row i
+ *            of the block: z_0 = 0, z_i = zigzag(v_i - v_{i-1}),
+ *            zigzag(d) = 2d for d >= 0, -2d - 1 for d < 0; w = bit length of
+ *            max z_i (0..17); words: (uint16)v_0 | w << 16, then w bit planes,
+ *            bit i of plane k = bit k of z_i.
+ *
  * Per-crystal full-resolution fill sum (the form Table 2's fill-by-fill sum
  * kernel suggests with one thread per crystal and sample, 54 x 560,000):
  *   Qx[c][x][t] += s[f][c][x][t] - P[f][c][x]   for t < len_f, over all fills f
@@ -262,6 +275,141 @@ int oracle_crystal_sum(const int16_t *samples, int32_t n_fills, int32_t n_calo, 
                 int64_t *qrow = q + ((int64_t)c * n_xtal + x) * pitch;
                 for (int64_t t = 0; t < len; ++t) qrow[t] += (int64_t)row[t] - ped;
             }
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------- packed pool stream */
+static void put_u32(uint8_t *p, uint32_t v)
+{
+    for (int k = 0; k < 4; ++k) p[k] = (uint8_t)(v >> (8 * k));
+}
+
+static void put_u64(uint8_t *p, uint64_t v)
+{
+    for (int k = 0; k < 8; ++k) p[k] = (uint8_t)(v >> (8 * k));
+}
+
+static uint32_t get_u32(const uint8_t *p)
+{
+    uint32_t v = 0;
+    for (int k = 0; k < 4; ++k) v |= (uint32_t)p[k] << (8 * k);
+    return v;
+}
+
+static uint64_t get_u64(const uint8_t *p)
+{
+    uint64_t v = 0;
+    for (int k = 0; k < 8; ++k) v |= (uint64_t)p[k] << (8 * k);
+    return v;
+}
+
+static uint32_t zigzag(int32_t d) { return d >= 0 ? 2u * (uint32_t)d : 2u * (uint32_t)(-(int64_t)d) - 1u; }
+
+static int32_t unzigzag(uint32_t z) { return (z & 1u) ? -(int32_t)((z + 1u) / 2u) : (int32_t)(z / 2u); }
+
+static int bit_length(uint32_t v)
+{
+    int n = 0;
+    while (v) {
+        ++n;
+        v >>= 1;
+    }
+    return n;
+}
+
+/* Block b, crystal x: the 32 samples (padded with the last row). */
+static void block_column(const int16_t *pool, int64_t rows, int32_t n_xtal, int64_t b, int32_t x, int32_t v[32])
+{
+    for (int i = 0; i < 32; ++i) {
+        int64_t r = 32 * b + i;
+        if (r >= rows) r = rows - 1;
+        v[i] = pool[r * n_xtal + x];
+    }
+}
+
+/* Pack pool[rows][n_xtal]; returns the stream's size, writing only the bytes
+ * that fit in cap (out may be NULL with cap 0 to ask for the size). */
+int64_t oracle_pack(const int16_t *pool, int64_t rows, int32_t n_xtal, uint8_t *out, int64_t cap)
+{
+    if (rows < 0 || n_xtal < 1 || cap < 0) return -1;
+    const int64_t nb = (rows + 31) / 32;
+    const int64_t head = 16 + 8 * (nb + 1);
+    int64_t pos = 0; /* payload bytes so far */
+    uint8_t w8[8];
+#define EMIT(off, nbytes, src)                                                                                   \
+    do {                                                                                                         \
+        for (int q_ = 0; q_ < (nbytes); ++q_)                                                                    \
+            if ((off) + q_ < cap) out[(off) + q_] = (src)[q_];                                                   \
+    } while (0)
+    put_u32(w8, 0x50514144u);
+    put_u32(w8 + 4, (uint32_t)n_xtal);
+    EMIT(0, 8, w8);
+    put_u64(w8, (uint64_t)rows);
+    EMIT(8, 8, w8);
+    for (int64_t b = 0; b < nb; ++b) {
+        put_u64(w8, (uint64_t)pos);
+        EMIT(16 + 8 * b, 8, w8);
+        for (int32_t x = 0; x < n_xtal; ++x) {
+            int32_t v[32];
+            uint32_t z[32];
+            block_column(pool, rows, n_xtal, b, x, v);
+            uint32_t zmax = 0;
+            z[0] = 0;
+            for (int i = 1; i < 32; ++i) {
+                z[i] = zigzag(v[i] - v[i - 1]);
+                if (z[i] > zmax) zmax = z[i];
+            }
+            const int w = bit_length(zmax);
+            put_u32(w8, (uint32_t)(uint16_t)v[0] | ((uint32_t)w << 16));
+            EMIT(head + pos, 4, w8);
+            pos += 4;
+            for (int k = 0; k < w; ++k) {
+                uint32_t plane = 0;
+                for (int i = 0; i < 32; ++i) plane |= ((z[i] >> k) & 1u) << i;
+                put_u32(w8, plane);
+                EMIT(head + pos, 4, w8);
+                pos += 4;
+            }
+        }
+    }
+    put_u64(w8, (uint64_t)pos);
+    EMIT(16 + 8 * nb, 8, w8);
+#undef EMIT
+    return head + pos;
+}
+
+/* Unpack a stream into pool_out[rows][n_xtal]; rows and n_xtal must match the
+ * header.  Returns 0, or -1 for a malformed stream. */
+int oracle_unpack(const uint8_t *in, int64_t bytes, int16_t *pool_out, int64_t rows, int32_t n_xtal)
+{
+    if (bytes < 16 || get_u32(in) != 0x50514144u || (int32_t)get_u32(in + 4) != n_xtal ||
+        (int64_t)get_u64(in + 8) != rows)
+        return -1;
+    const int64_t nb = (rows + 31) / 32;
+    const int64_t head = 16 + 8 * (nb + 1);
+    if (bytes < head) return -1;
+    for (int64_t b = 0; b < nb; ++b) {
+        int64_t pos = head + (int64_t)get_u64(in + 16 + 8 * b);
+        for (int32_t x = 0; x < n_xtal; ++x) {
+            if (pos + 4 > bytes) return -1;
+            const uint32_t h = get_u32(in + pos);
+            pos += 4;
+            const int w = (int)(h >> 16);
+            if (w > 17 || pos + 4 * (int64_t)w > bytes) return -1;
+            uint32_t z[32] = {0};
+            for (int k = 0; k < w; ++k) {
+                const uint32_t plane = get_u32(in + pos);
+                pos += 4;
+                for (int i = 0; i < 32; ++i) z[i] |= ((plane >> i) & 1u) << k;
+            }
+            int32_t v = (int16_t)(h & 0xffffu);
+            for (int i = 0; i < 32; ++i) {
+                if (i > 0) v += unzigzag(z[i]);
+                const int64_t r = 32 * b + i;
+                if (r < rows) pool_out[r * n_xtal + x] = (int16_t)v;
+            }
+        }
     }
     return 0;
 }

@@ -240,9 +240,46 @@ def pin_crystal_sum_matches_decimated_q(orc):
         assert np.array_equal(got, want), D
 
 
+def pin_pack_golden(orc):
+    """The packed stream of a hand-derived 3-row pool, word by word."""
+    n = 0
+    for fn in sorted(glob.glob(os.path.join(GOLDEN, "*.json"))):
+        g = json.load(open(fn))
+        if g.get("kind") != "pack":
+            continue
+        pool = np.array(g["pool"], np.int16)
+        st = orc.pack(pool)
+        assert st.size % 4 == 0 and st.view("<u4").tolist() == g["expected_words"], os.path.basename(fn)
+        assert np.array_equal(orc.unpack(st, *pool.shape), pool)
+        n += 1
+    assert n >= 1, "pack fixture missing"
+
+
+def pin_pack_round_trip_and_size(orc):
+    """Lossless for any int16 rows (extremes give 17-bit differences), and the
+    size is the header, the offsets and one head word plus w planes per crystal
+    and block."""
+    rng = np.random.default_rng(21)
+    cases = [rng.integers(-32768, 32768, size=(77, 3)), np.tile([[-32768], [32767]], (20, 5)),
+             np.full((64, 54), 1800), rng.integers(1790, 1811, size=(200, 54)), np.zeros((0, 4))]
+    for pool in cases:
+        pool = np.asarray(pool).astype(np.int16)
+        rows, X = pool.shape
+        st = orc.pack(pool)
+        assert np.array_equal(orc.unpack(st, rows, X), pool)
+        nb = -(-rows // 32)
+        words = 0
+        for b in range(nb):
+            blk = np.concatenate([pool[32 * b: 32 * b + 32], np.repeat(pool[-1:], max(0, 32 * b + 32 - rows), 0)])
+            d = np.diff(blk.astype(np.int64), axis=0)
+            z = np.where(d >= 0, 2 * d, -2 * d - 1)
+            words += sum(1 + int(m).bit_length() for m in z.max(axis=0))
+        assert st.size == 16 + 8 * (nb + 1) + 4 * words
+
+
 PINS = [pin_golden, pin_single_crossing, pin_merge_boundary, pin_threshold_strict_and_extremes,
         pin_pedestal_rounding, pin_decimation, pin_against_brute, pin_fill_sum_accumulates,
-        pin_crystal_sum_golden, pin_crystal_sum_matches_decimated_q]
+        pin_crystal_sum_golden, pin_crystal_sum_matches_decimated_q, pin_pack_golden, pin_pack_round_trip_and_size]
 
 
 # ---------------------------------------------------------------- invariants on any output

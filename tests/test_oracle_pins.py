@@ -152,6 +152,9 @@ MUTANTS = {
     "xtal_sum_ignores_fill_len": ("for (int64_t t = 0; t < len; ++t) qrow[t]", "for (int64_t t = 0; t < pitch; ++t) qrow[t]"),
     "xtal_sum_rows_transposed": ("int64_t *qrow = q + ((int64_t)c * n_xtal + x) * pitch;",
                                  "int64_t *qrow = q + ((int64_t)x * n_calo + c) * pitch;"),
+    "pack_zigzag_off_by_one": ("2u * (uint32_t)(-(int64_t)d) - 1u", "2u * (uint32_t)(-(int64_t)d)"),
+    "pack_pads_with_zero": ("if (r >= rows) r = rows - 1;", "if (r >= rows) { v[i] = 0; continue; }"),
+    "pack_width_short": ("const int w = bit_length(zmax);", "const int w = zmax ? bit_length(zmax) - 1 : 0;"),
 }
 
 
