@@ -510,6 +510,40 @@ int daq_crystal_sum_workspace_size(int n_calo, int n_xtal, int n_fills, size_t *
 int daq_crystal_sum(const int16_t *samples, int n_calo, int n_xtal, int64_t n_samples, int n_fills,
                     const daq_params *params, int64_t *q_xtal);
 
+/*
+ * Lossless packing of pool rows (Sec. 2: the frontend compresses island data
+ * losslessly before sending it to the event builder; the method is not named,
+ * the format below is this library's).  Stream (little-endian):
+ *   header   u32 magic 0x50514144, u32 n_xtal, u64 rows
+ *   offsets  u64[n_blocks + 1], n_blocks = ceil(rows / 32): byte offset of each
+ *            block's payload from the payload start (the last = payload size)
+ *   payload  block b = rows [32b, 32b + 32), the last block padded with copies
+ *            of its final row; per crystal x, with v_i the crystal's sample in
+ *            row i of the block: z_0 = 0, z_i = zigzag(v_i - v_{i-1}) (2d for
+ *            d >= 0, -2d - 1 otherwise), w = bit length of max z_i (0..17); the
+ *            words (uint16)v_0 | w << 16, then w bit planes (bit i of plane k =
+ *            bit k of z_i).
+ * daq_pack_bound          worst-case stream bytes for rows x n_xtal (-1 if invalid).
+ * daq_pack_workspace_size device scratch daq_pack_pool needs.
+ * daq_pack_pool           pack device pool[rows][n_xtal] (n_xtal <= 64) into
+ *                         device out (16-byte aligned, out_cap bytes) on
+ *                         `stream`; *out_bytes (device int64) receives the
+ *                         stream's size - bytes past out_cap are not written,
+ *                         so out_cap >= daq_pack_bound() is always enough.
+ * daq_unpack_pool         decode a stream of in_bytes bytes into device
+ *                         pool_out[rows][n_xtal]; *err (device int32) is set
+ *                         to 0, or to a non-zero code when the header does not
+ *                         match (1) or the stream is malformed or cut short (2).
+ * All asynchronous on `stream` (cudaStream_t); DAQ_EINVAL / DAQ_EUNSUPPORTED
+ * for bad arguments before any device work.
+ */
+int64_t daq_pack_bound(int64_t rows, int n_xtal);
+int daq_pack_workspace_size(int64_t rows, int n_xtal, size_t *bytes);
+int daq_pack_pool(const int16_t *pool, int64_t rows, int n_xtal, void *out, int64_t out_cap, int64_t *out_bytes,
+                  void *workspace, size_t workspace_bytes, void *stream);
+int daq_unpack_pool(const void *in, int64_t in_bytes, int64_t rows, int n_xtal, int16_t *pool_out, int32_t *err,
+                    void *stream);
+
 /* Upper bound on the tiles of a call with these sizes and parameters (rows of
  * the trace buffer); 0 on invalid arguments. */
 int64_t daq_trace_tiles(int n_calo, int n_xtal, int64_t n_samples, int n_fills, const daq_params *params);

@@ -149,6 +149,14 @@ def lib():
             L.daq_crystal_sum_workspace_size.restype = i32
             L.daq_crystal_sum.argtypes = [vp, i32, i32, i64, i32, ctypes.POINTER(DaqParams), vp]
             L.daq_crystal_sum.restype = i32
+            L.daq_pack_bound.argtypes = [i64, i32]
+            L.daq_pack_bound.restype = i64
+            L.daq_pack_workspace_size.argtypes = [i64, i32, ctypes.POINTER(ctypes.c_size_t)]
+            L.daq_pack_workspace_size.restype = i32
+            L.daq_pack_pool.argtypes = [vp, i64, i32, vp, i64, vp, vp, ctypes.c_size_t, vp]
+            L.daq_pack_pool.restype = i32
+            L.daq_unpack_pool.argtypes = [vp, i64, i64, i32, vp, vp, vp]
+            L.daq_unpack_pool.restype = i32
             L.daq_server_create.argtypes = [ctypes.POINTER(DaqServerConfig), ctypes.POINTER(vp)]
             L.daq_server_create.restype = i32
             L.daq_server_submit.argtypes = [vp, vp, i32, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(i64)]
@@ -296,6 +304,66 @@ def crystal_sum(samples, q=None, ped_samples: int = 100, fill_len=None, stream=N
     if rc != DAQ_OK:
         raise DaqError(rc, "daq_crystal_sum")
     return q
+
+
+def daq_pack_bound(rows: int, n_xtal: int) -> int:
+    return int(lib().daq_pack_bound(rows, n_xtal))
+
+
+def daq_pack_workspace_size(rows: int, n_xtal: int) -> int:
+    out = ctypes.c_size_t(0)
+    rc = lib().daq_pack_workspace_size(rows, n_xtal, ctypes.byref(out))
+    if rc:
+        raise DaqError(rc, "daq_pack_workspace_size")
+    return int(out.value)
+
+
+def daq_pack_pool(pool_ptr, rows, n_xtal, out_ptr, out_cap, out_bytes_ptr, ws_ptr, ws_bytes, stream_ptr) -> int:
+    return int(lib().daq_pack_pool(pool_ptr, rows, n_xtal, out_ptr, out_cap, out_bytes_ptr, ws_ptr, ws_bytes,
+                                   stream_ptr))
+
+
+def daq_unpack_pool(in_ptr, in_bytes, rows, n_xtal, out_ptr, err_ptr, stream_ptr) -> int:
+    return int(lib().daq_unpack_pool(in_ptr, in_bytes, rows, n_xtal, out_ptr, err_ptr, stream_ptr))
+
+
+def pack_pool(pool, rows: int | None = None, stream=None, out=None, workspace=None):
+    """Pack the first `rows` rows of a CUDA int16 pool [rows][X].  Returns
+    (stream uint8 tensor view of its exact size, size)."""
+    import torch
+    rows = pool.shape[0] if rows is None else int(rows)
+    X = int(pool.shape[1])
+    dev = pool.device
+    cap = daq_pack_bound(rows, X)
+    if out is None or out.numel() < cap:
+        out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    need = daq_pack_workspace_size(rows, X)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    nbytes = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev) if stream is None else stream
+    rc = daq_pack_pool(pool.data_ptr(), rows, X, out.data_ptr(), out.numel(), nbytes.data_ptr(), workspace.data_ptr(),
+                       workspace.numel(), stream.cuda_stream)
+    if rc != DAQ_OK:
+        raise DaqError(rc, "daq_pack_pool")
+    n = int(nbytes.item())
+    return out[:n], n
+
+
+def unpack_pool(packed, rows: int, n_xtal: int, stream=None):
+    """Decode a packed stream (CUDA uint8 tensor) into a new int16 [rows][n_xtal] tensor."""
+    import torch
+    dev = packed.device
+    out = torch.empty((max(1, rows), n_xtal), dtype=torch.int16, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev) if stream is None else stream
+    rc = daq_unpack_pool(packed.data_ptr(), packed.numel(), rows, n_xtal, out.data_ptr(), err.data_ptr(),
+                         stream.cuda_stream)
+    if rc != DAQ_OK:
+        raise DaqError(rc, "daq_unpack_pool")
+    if int(err.item()) != 0:
+        raise DaqError(DAQ_EINVAL, f"daq_unpack_pool: malformed stream (code {int(err.item())})")
+    return out[:rows]
 
 
 def daq_status_from_counts(counts_host) -> int:

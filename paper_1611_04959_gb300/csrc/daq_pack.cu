@@ -1,0 +1,367 @@
+// Lossless packing of pool rows on the GPU (Sec. 2: the frontend compresses
+// island data losslessly before event building).  Stream format:
+//   header   u32 magic 0x50514144, u32 n_xtal, u64 rows
+//   offsets  u64[n_blocks + 1], n_blocks = ceil(rows / 32): byte offset of each
+//            block's payload from the payload start (the last = payload size)
+//   payload  block b = rows [32b, 32b + 32), the last block padded with copies
+//            of the final row; per crystal x, with v_i the sample of row i:
+//            z_0 = 0, z_i = zigzag(v_i - v_{i-1}) (2d for d >= 0, -2d - 1 else),
+//            w = bit length of max z_i (0..17); words: (uint16)v_0 | w << 16,
+//            then w bit planes, bit i of plane k = bit k of z_i.
+// Consecutive pool rows are consecutive samples of an island, so the row to
+// row differences of a crystal are small (noise, pulse edges) and a block's
+// crystal column typically needs a few bits per sample instead of 16.
+//
+// One warp per block: the block's rows are copied to shared memory (row pitch
+// an odd number of words, so a warp reading one crystal down 32 rows hits 32
+// banks), each crystal column's differences are formed with one shuffle, its
+// width with one max-reduction and its planes with one ballot each.  A size
+// pass, an exclusive scan of the block sizes (three kernels) and a write pass;
+// the decoder is the same walk backwards (ballots become bit extraction, the
+// differences an inclusive warp scan).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "daq.h"
+
+namespace daq_pack {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarps = 8;
+constexpr int kThreads = 32 * kWarps;
+constexpr int kMaxX = 64;
+constexpr uint32_t kMagic = 0x50514144u;
+constexpr int kScanPer = 4;
+constexpr int kScanChunk = kThreads * kScanPer;
+
+// shared-memory row pitch (int16 elements): an odd number of 32-bit words
+__host__ __device__ __forceinline__ int row_pitch(int X) { return 2 * (((X + 1) / 2) | 1); }
+
+__device__ __forceinline__ uint32_t zigzag(int32_t d) { return d >= 0 ? 2u * (uint32_t)d : 2u * (uint32_t)(-d) - 1u; }
+
+__device__ __forceinline__ int32_t unzigzag(uint32_t z) { return (z & 1u) ? -(int32_t)((z + 1u) >> 1) : (int32_t)(z >> 1); }
+
+// Copy block b's rows into the warp's shared rows (padding rows past the end
+// with the final row).  Returns the number of real rows.
+__device__ __forceinline__ int load_block(const int16_t *pool, long long rows, int X, long long b, int16_t *sm,
+                                          int lane)
+{
+    const long long r0 = 32ll * b;
+    const int nv = (int)min(32ll, rows - r0);
+    const int P = row_pitch(X);
+    const int16_t *src = pool + r0 * X;
+    const int n = nv * X;
+    for (int e = lane; e < n; e += 32) {
+        const int i = e / X, x = e - i * X;
+        sm[i * P + x] = src[e];
+    }
+    __syncwarp();
+    for (int e = lane; e < (32 - nv) * X; e += 32) {
+        const int i = nv + e / X, x = e % X;
+        sm[i * P + x] = sm[(nv - 1) * P + x];
+    }
+    __syncwarp();
+    return nv;
+}
+
+__global__ void __launch_bounds__(kThreads) pack_size_kernel(const int16_t *pool, long long rows, int X,
+                                                             long long nb, unsigned long long *sizes)
+{
+    __shared__ int16_t sm_all[kWarps][32 * 2 * ((kMaxX / 2) | 1)];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int16_t *sm = sm_all[warp];
+    const int P = row_pitch(X);
+    for (long long b = (long long)blockIdx.x * kWarps + warp; b < nb; b += (long long)gridDim.x * kWarps) {
+        load_block(pool, rows, X, b, sm, lane);
+        unsigned words = 0;
+        for (int x = 0; x < X; ++x) {
+            const int32_t v = sm[lane * P + x];
+            const int32_t prev = __shfl_up_sync(kFull, v, 1);
+            const uint32_t z = lane ? zigzag(v - prev) : 0u;
+            const uint32_t m = __reduce_max_sync(kFull, z);
+            words += 1u + (m ? 32u - __clz(m) : 0u);
+        }
+        if (lane == 0) sizes[b] = 4ull * words;
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ exclusive scan of the block sizes
+__global__ void __launch_bounds__(kThreads) scan_reduce_kernel(const unsigned long long *v, long long n,
+                                                               unsigned long long *chunk)
+{
+    __shared__ unsigned long long s[kWarps];
+    const long long base = (long long)blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+    unsigned long long t = 0;
+    for (int i = 0; i < kScanPer; ++i)
+        if (base + i < n) t += v[base + i];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(kFull, t, d);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long a = 0;
+        for (int w = 0; w < kWarps; ++w) a += s[w];
+        chunk[blockIdx.x] = a;
+    }
+}
+
+// One block: chunk sums -> exclusive prefixes (in place); chunk[n_chunks] = total.
+__global__ void __launch_bounds__(1024) scan_top_kernel(unsigned long long *chunk, long long n_chunks)
+{
+    __shared__ unsigned long long s[32];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long base = 0; base < n_chunks; base += 1024) {
+        const long long i = base + threadIdx.x;
+        const unsigned long long v = i < n_chunks ? chunk[i] : 0ull;
+        unsigned long long x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) s[warp] = x;
+        __syncthreads();
+        unsigned long long pre = carry;
+        for (int w = 0; w < warp; ++w) pre += s[w];
+        if (i < n_chunks) chunk[i] = pre + x - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = pre + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) chunk[n_chunks] = carry;
+}
+
+// offsets[b] = exclusive prefix (workspace, and the stream's table when it
+// fits), offsets[nb] = payload size, *out_bytes = whole stream size.
+__global__ void __launch_bounds__(kThreads) scan_apply_kernel(const unsigned long long *v, long long n,
+                                                              const unsigned long long *chunk,
+                                                              unsigned long long *offs, unsigned char *out,
+                                                              long long cap, long long *out_bytes)
+{
+    __shared__ unsigned long long s[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long base = (long long)blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+    unsigned long long loc[kScanPer], t = 0;
+    for (int i = 0; i < kScanPer; ++i) {
+        loc[i] = base + i < n ? v[base + i] : 0ull;
+        t += loc[i];
+    }
+    unsigned long long x = t;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) s[warp] = x;
+    __syncthreads();
+    unsigned long long pre = chunk[blockIdx.x];
+    for (int w = 0; w < warp; ++w) pre += s[w];
+    pre += x - t;
+    const long long table = 16;  // the offsets table starts after the 16-byte header
+    for (int i = 0; i < kScanPer; ++i) {
+        const long long k = base + i;  // entries 0..n (entry n: the payload size)
+        if (k <= n) {
+            offs[k] = pre;
+            if (table + 8 * k + 8 <= cap) reinterpret_cast<unsigned long long *>(out + table)[k] = pre;
+            if (k == n) *out_bytes = 16 + 8 * (n + 1) + (long long)pre;
+        }
+        pre += loc[i];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *pool, long long rows, int X, long long nb,
+                                                              const unsigned long long *offs, unsigned char *out,
+                                                              long long cap)
+{
+    __shared__ int16_t sm_all[kWarps][32 * 2 * ((kMaxX / 2) | 1)];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int16_t *sm = sm_all[warp];
+    const int P = row_pitch(X);
+    const long long head = 16 + 8 * (nb + 1);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && cap >= 16) {
+        uint32_t *h = reinterpret_cast<uint32_t *>(out);
+        h[0] = kMagic;
+        h[1] = (uint32_t)X;
+        reinterpret_cast<unsigned long long *>(out)[1] = (unsigned long long)rows;
+    }
+    for (long long b = (long long)blockIdx.x * kWarps + warp; b < nb; b += (long long)gridDim.x * kWarps) {
+        load_block(pool, rows, X, b, sm, lane);
+        long long pos = head + (long long)offs[b];  // bytes, a multiple of 4
+        for (int x = 0; x < X; ++x) {
+            const int32_t v = sm[lane * P + x];
+            const int32_t prev = __shfl_up_sync(kFull, v, 1);
+            const uint32_t z = lane ? zigzag(v - prev) : 0u;
+            const uint32_t m = __reduce_max_sync(kFull, z);
+            const int w = m ? 32 - __clz(m) : 0;
+            const int32_t v0 = __shfl_sync(kFull, v, 0);
+            uint32_t mine = (uint32_t)(uint16_t)v0 | ((uint32_t)w << 16);  // lane 0: head word
+            for (int k = 0; k < w; ++k) {
+                const uint32_t plane = __ballot_sync(kFull, (z >> k) & 1u);
+                if (lane == k + 1) mine = plane;
+            }
+            if (lane <= w && pos + 4ll * lane + 4 <= cap)
+                reinterpret_cast<uint32_t *>(out + pos)[lane] = mine;
+            pos += 4ll * (1 + w);
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) unpack_kernel(const unsigned char *in, long long in_bytes, long long rows,
+                                                          int X, long long nb, int16_t *pool_out, int *err)
+{
+    __shared__ int16_t sm_all[kWarps][32 * 2 * ((kMaxX / 2) | 1)];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int16_t *sm = sm_all[warp];
+    const int P = row_pitch(X);
+    const long long head = 16 + 8 * (nb + 1);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint32_t *h = reinterpret_cast<const uint32_t *>(in);
+        if (h[0] != kMagic || h[1] != (uint32_t)X || reinterpret_cast<const unsigned long long *>(in)[1] !=
+                                                             (unsigned long long)rows)
+            atomicOr(err, 1);
+    }
+    const unsigned long long *offs = reinterpret_cast<const unsigned long long *>(in + 16);
+    for (long long b = (long long)blockIdx.x * kWarps + warp; b < nb; b += (long long)gridDim.x * kWarps) {
+        if (head > in_bytes) {  // the offsets table itself is cut short
+            if (lane == 0) atomicOr(err, 2);
+            continue;
+        }
+        const unsigned long long off = offs[b];
+        bool bad = off > (unsigned long long)(in_bytes - head) || (off & 3ull);
+        long long pos = head + (long long)(bad ? 0ull : off);  // bytes read so far end at pos
+        const uint32_t *p = reinterpret_cast<const uint32_t *>(in + pos);
+        for (int x = 0; x < X && !bad; ++x) {
+            if (pos + 4 > in_bytes) {
+                bad = true;
+                break;
+            }
+            const uint32_t h = p[0];
+            const int w = (int)(h >> 16);
+            if (w > 17 || pos + 4ll * (1 + w) > in_bytes) {
+                bad = true;
+                break;
+            }
+            pos += 4ll * (1 + w);
+            uint32_t z = 0;
+            for (int k = 0; k < w; ++k) z |= ((p[1 + k] >> lane) & 1u) << k;
+            int32_t d = lane ? unzigzag(z) : 0;
+#pragma unroll
+            for (int s = 1; s < 32; s <<= 1) {
+                const int32_t y = __shfl_up_sync(kFull, d, s);
+                if (lane >= s) d += y;
+            }
+            sm[lane * P + x] = (int16_t)((int32_t)(int16_t)(h & 0xffffu) + d);
+            p += 1 + w;
+        }
+        if (bad) {
+            if (lane == 0) atomicOr(err, 2);
+            continue;
+        }
+        __syncwarp();
+        const long long r0 = 32ll * b;
+        const int nv = (int)min(32ll, rows - r0);
+        int16_t *dst = pool_out + r0 * X;
+        for (int e = lane; e < nv * X; e += 32) {
+            const int i = e / X, x = e - i * X;
+            dst[e] = sm[i * P + x];
+        }
+        __syncwarp();
+    }
+}
+
+int grid_blocks(long long nb)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (nb + kWarps - 1) / kWarps;
+    return (int)std::max<long long>(1, std::min<long long>(want, (long long)std::max(sms, 1) * 16));
+}
+
+struct PackWs {
+    size_t sizes, offs, chunk, total;
+};
+
+PackWs pack_ws(long long nb)
+{
+    auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+    PackWs w;
+    w.sizes = 0;
+    w.offs = up(8 * (size_t)std::max<long long>(nb, 1));
+    w.chunk = up(w.offs + 8 * (size_t)(nb + 1));
+    const long long n_chunks = (nb + kScanChunk - 1) / kScanChunk;
+    w.total = up(w.chunk + 8 * (size_t)(n_chunks + 1));
+    return w;
+}
+
+}  // namespace daq_pack
+
+using namespace daq_pack;
+
+extern "C" {
+
+int64_t daq_pack_bound(int64_t rows, int n_xtal)
+{
+    if (rows < 0 || n_xtal < 1 || n_xtal > kMaxX) return -1;
+    const int64_t nb = (rows + 31) / 32;
+    return 16 + 8 * (nb + 1) + nb * (int64_t)n_xtal * 4 * 18;
+}
+
+int daq_pack_workspace_size(int64_t rows, int n_xtal, size_t *bytes)
+{
+    if (!bytes || rows < 0 || n_xtal < 1 || n_xtal > kMaxX) return DAQ_EINVAL;
+    *bytes = pack_ws((rows + 31) / 32).total;
+    return DAQ_OK;
+}
+
+int daq_pack_pool(const int16_t *pool, int64_t rows, int n_xtal, void *out, int64_t out_cap, int64_t *out_bytes,
+                  void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (rows < 0 || n_xtal < 1 || out_cap < 0 || !out_bytes || (rows > 0 && !pool)) return DAQ_EINVAL;
+    if (n_xtal > kMaxX) return DAQ_EUNSUPPORTED;
+    if ((out_cap > 0 && !out) || (reinterpret_cast<uintptr_t>(out) & 15) || (reinterpret_cast<uintptr_t>(out_bytes) & 7))
+        return DAQ_EINVAL;
+    const long long nb = (rows + 31) / 32;
+    const PackWs w = pack_ws(nb);
+    if (!workspace || workspace_bytes < w.total || (reinterpret_cast<uintptr_t>(workspace) & 15)) return DAQ_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    auto *sizes = reinterpret_cast<unsigned long long *>(ws + w.sizes);
+    auto *offs = reinterpret_cast<unsigned long long *>(ws + w.offs);
+    auto *chunk = reinterpret_cast<unsigned long long *>(ws + w.chunk);
+    unsigned char *o = static_cast<unsigned char *>(out);
+    const long long n_apply = nb / kScanChunk + 1;  // blocks covering entries 0..nb
+    if (nb > 0) pack_size_kernel<<<grid_blocks(nb), kThreads, 0, s>>>(pool, rows, n_xtal, nb, sizes);
+    if (nb > 0) scan_reduce_kernel<<<(unsigned)((nb + kScanChunk - 1) / kScanChunk), kThreads, 0, s>>>(sizes, nb, chunk);
+    else if (cudaMemsetAsync(chunk, 0, 8, s) != cudaSuccess) return DAQ_ECUDA;
+    scan_top_kernel<<<1, 1024, 0, s>>>(chunk, nb > 0 ? (nb + kScanChunk - 1) / kScanChunk : 0);
+    scan_apply_kernel<<<(unsigned)n_apply, kThreads, 0, s>>>(sizes, nb, chunk, offs, o, out_cap,
+                                                             reinterpret_cast<long long *>(out_bytes));
+    pack_write_kernel<<<grid_blocks(std::max<long long>(nb, 1)), kThreads, 0, s>>>(pool, rows, n_xtal, nb, offs, o,
+                                                                                   out_cap);
+    return cudaGetLastError() == cudaSuccess ? DAQ_OK : DAQ_ECUDA;
+}
+
+int daq_unpack_pool(const void *in, int64_t in_bytes, int64_t rows, int n_xtal, int16_t *pool_out, int32_t *err,
+                    void *stream)
+{
+    if (!in || in_bytes < 16 || rows < 0 || n_xtal < 1 || !err || (rows > 0 && !pool_out) ||
+        (reinterpret_cast<uintptr_t>(in) & 15))
+        return DAQ_EINVAL;
+    if (n_xtal > kMaxX) return DAQ_EUNSUPPORTED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(err, 0, sizeof(int32_t), s) != cudaSuccess) return DAQ_ECUDA;
+    const long long nb = (rows + 31) / 32;
+    unpack_kernel<<<grid_blocks(std::max<long long>(nb, 1)), kThreads, 0, s>>>(
+        static_cast<const unsigned char *>(in), in_bytes, rows, n_xtal, nb, pool_out, err);
+    return cudaGetLastError() == cudaSuccess ? DAQ_OK : DAQ_ECUDA;
+}
+
+}  // extern "C"

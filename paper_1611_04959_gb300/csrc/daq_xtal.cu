@@ -18,7 +18,7 @@
 
 #include "daq.h"
 
-namespace {
+namespace daq_xtal {
 
 constexpr int kThreads = 256;
 
@@ -44,7 +44,8 @@ __device__ __forceinline__ long long floor_div_ll(long long a, long long b)
     return q;
 }
 
-// Fill lengths (clamped; out-of-range ones flagged) and every row's pedestal.
+// Fill lengths (clamped; out-of-range ones flagged in *status, cleared by the
+// host before the launch) and every row's pedestal.
 __global__ void __launch_bounds__(kThreads) xtal_prepare_kernel(const int16_t *samples, int n_fills, int n_calo,
                                                                 int n_xtal, int64_t pitch, const int32_t *fill_len,
                                                                 int ped_samples, int32_t *lens, int32_t *ped,
@@ -53,7 +54,6 @@ __global__ void __launch_bounds__(kThreads) xtal_prepare_kernel(const int16_t *s
     const int lane = threadIdx.x & 31;
     const long long gw = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * kThreads) >> 5;
-    if (gw == 0 && lane == 0) *status = 0ull;
     for (long long f = (long long)blockIdx.x * kThreads + threadIdx.x; f < n_fills; f += (long long)gridDim.x * kThreads) {
         long long len = fill_len ? (long long)fill_len[f] : pitch;
         if (len < 0 || len > pitch) {
@@ -140,7 +140,9 @@ int grid_for(long long work)
     return (int)std::max<long long>(1, std::min<long long>(want, (long long)std::max(sms, 1) * 8));
 }
 
-}  // namespace
+}  // namespace daq_xtal
+
+using namespace daq_xtal;
 
 extern "C" {
 
@@ -169,6 +171,7 @@ int daq_crystal_sum(const int16_t *samples, int n_calo, int n_xtal, int64_t n_sa
     unsigned long long *status = reinterpret_cast<unsigned long long *>(ws + l.status);
     int32_t *lens = reinterpret_cast<int32_t *>(ws + l.lens);
     int32_t *ped = reinterpret_cast<int32_t *>(ws + l.ped);
+    if (cudaMemsetAsync(status, 0, sizeof(*status), s) != cudaSuccess) return DAQ_ECUDA;
     xtal_prepare_kernel<<<grid_for(std::max<int64_t>(n_rows * 32, n_fills)), kThreads, 0, s>>>(
         samples, n_fills, n_calo, n_xtal, n_samples, params->fill_len, params->ped_samples, lens, ped, status);
     if (cudaGetLastError() != cudaSuccess) return DAQ_ECUDA;
