@@ -316,6 +316,10 @@ def bench_gb300(args, ws, rank, local):
     if not args.no_sparse and not args.quick:
         result["sparse"] = bench_sparse(args, torch, dev, daq, synth, W)
 
+    # ---- lossless packing of the pool rows
+    if not args.no_pack and not args.quick:
+        result["pack"] = bench_pack(args, torch, dev, daq, out.pool, n_rows)
+
     # ---- per-crystal full-resolution fill sum
     if not args.no_crystal_sum and not args.quick:
         result["crystal_sum"] = bench_crystal_sum(args, torch, dev, daq, samples)
@@ -371,13 +375,39 @@ def bench_gb300(args, ws, rank, local):
         bw = copy_bandwidth(torch, dev, host, samples, pool_h, out.pool, int(counts_h[1]))
         e2e_bound = raw_bytes / max(raw_bytes / bw["h2d_gbs"], d2h / bw["d2h_gbs"],
                                     (raw_bytes + d2h) / bw["bidir_gbs"]) if bw["h2d_gbs"] else None
+        # the same through the packed host form (pool rows leave the GPU packed)
+        pcap = daq.daq_pack_bound(rows_cap, X) + 64 * 8192
+        pdev = torch.empty(pcap, dtype=torch.uint8, device=dev)
+        phost = torch.empty(pcap, dtype=torch.uint8).pin_memory()
+        pbytes = torch.zeros(1, dtype=torch.int64)
+        pp_ = make_p()[0]
+        pp_.workspace, pp_.workspace_bytes = workspace.data_ptr(), wsb
+        pp_.flags |= daq.DAQ_PACK_POOL
+        io.packed_dev, io.packed_dev_cap = pdev.data_ptr(), pcap
+        io.packed_host, io.packed_host_cap, io.packed_bytes_host = phost.data_ptr(), pcap, pbytes.data_ptr()
+        for _ in range(2):
+            rc = daq.daq_process_fills_host(C, X, N, F, pp_, isl, q.data_ptr(), io)
+            assert rc == daq.DAQ_OK, rc
+        barrier()
+        e0.record(stream)
+        for _ in range(Ke):
+            daq.daq_process_fills_host(C, X, N, F, pp_, isl, q.data_ptr(), io)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        _, pms, pk_value = replicas.aggregate(Ke * raw_bytes, e0.elapsed_time(e1), dev)
+        pk_d2h = 32 + int(counts_h[0]) * 24 + int(pbytes.item())
+        del pdev, phost
         result["e2e"] = {"value": round(e2e_value, 2), "unit": UNIT,
                          "h2d_bytes_per_step": raw_bytes, "d2h_bytes_per_step": d2h, "steps": Ke,
                          "ms_per_step": round(ems / Ke, 3),
                          "api": "daq_process_fills_host (pinned host buffers; copy-in, processing and copy-out "
                                 "pipelined over calorimeter chunks)",
                          "copy_bandwidth": bw,
-                         "bound_gbs": None if e2e_bound is None else round(e2e_bound, 2)}
+                         "bound_gbs": None if e2e_bound is None else round(e2e_bound, 2),
+                         "packed": {"value": round(pk_value, 2), "unit": UNIT, "ms_per_step": round(pms / Ke, 3),
+                                    "h2d_bytes_per_step": raw_bytes, "d2h_bytes_per_step": pk_d2h,
+                                    "api": "daq_process_fills_host with DAQ_PACK_POOL (pool rows packed losslessly "
+                                           "on the GPU before the copy back)"}}
 
     # ---- CPU baseline: the oracle on a bounded sample of the same fill (rank 0)
     if rank == 0 and not args.no_cpu_baseline:
@@ -650,6 +680,47 @@ def bench_crystal_sum(args, torch, dev, daq, samples) -> dict:
             "gpu_launches": 2 * K}
 
 
+def bench_pack(args, torch, dev, daq, pool, rows: int) -> dict:
+    """Lossless packing of the full fill's pool rows (what leaves the GPU)."""
+    X = int(pool.shape[1])
+    cap = daq.daq_pack_bound(rows, X)
+    out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    need = daq.daq_pack_workspace_size(rows, X)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    nbytes = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.Stream(dev)
+
+    def call():
+        rc = daq.daq_pack_pool(pool.data_ptr(), rows, X, out.data_ptr(), cap, nbytes.data_ptr(), ws.data_ptr(),
+                               need, stream.cuda_stream)
+        assert rc == daq.DAQ_OK, rc
+
+    for _ in range(3):
+        call()
+    K = max(3, min(args.steps, args.pack_steps))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(K):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / K
+    n = int(nbytes.item())
+    raw = rows * X * 2
+    alg = 2 * raw + n        # the pool is read by the size pass and by the write pass
+    peak = measured_peaks()[0]
+    del out, ws
+    torch.cuda.empty_cache()
+    return {"value": round(raw / (ms * 1e-3) / 1e9, 2), "unit": "GB/s of pool rows packed", "steps": K,
+            "ms_per_fill": round(ms, 4), "pool_bytes": raw, "packed_bytes": n,
+            "compression_ratio": round(raw / max(1, n), 3),
+            "workload": "pool rows of the full fill (24 x 54 x 560,000, T=30, pre=8, post=24)",
+            "roofline": {"bound": "hbm", "achieved": round(alg / (ms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4), "algorithmic_bytes_per_launch": alg},
+            "gpu_launches": 5 * K}
+
+
 THRESHOLDS = (5, 10, 15, 20, 30, 50, 100, 300, 1000)
 
 
@@ -842,6 +913,8 @@ def main():
     ap.add_argument("--no-threshold-scan", action="store_true", help="skip the island-efficiency threshold scan")
     ap.add_argument("--no-crystal-sum", action="store_true", help="skip the per-crystal full-resolution fill sum")
     ap.add_argument("--crystal-steps", type=int, default=50)
+    ap.add_argument("--no-pack", action="store_true", help="skip the pool-packing measurement")
+    ap.add_argument("--pack-steps", type=int, default=50)
     ap.add_argument("--sparse-steps", type=int, default=1000)
     ap.add_argument("--serve-pool", type=int, default=4, help="distinct device fills the served stream cycles over")
     ap.add_argument("--serve-fills", type=int, default=1024, help="fills per served run at 10x and 100x")

@@ -46,6 +46,7 @@ enum daq_status {
 #define DAQ_SKIP_Q 1u        /* leave qhist_inout untouched */
 #define DAQ_SKIP_ISLANDS 2u  /* compute counts, write no island records, pool rows or pedestals */
 #define DAQ_SYNC 4u          /* wait for the stream, then return the device-side status */
+#define DAQ_PACK_POOL 8u     /* daq_process_fills_host: return the pool rows packed (see daq_pack_pool) */
 
 /* Bits of counts[2] (device-side status, OR-ed by the kernels). */
 #define DAQ_DEV_HDR_OVERFLOW 1
@@ -215,6 +216,17 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
  *                  records, pool rows and pedestals (pedestal_host may be NULL);
  *                  at most *_cap entries are copied.
  *   counts_host    host int64[4], receives counts (see daq_islands).
+ *   With DAQ_PACK_POOL in params->flags the pool rows come back packed instead
+ *   (pool_host is not used):
+ *   packed_dev     device scratch for the packed streams, 16-byte aligned, of
+ *                  at least daq_pack_bound(n_fills * n_calo * n_samples,
+ *                  n_xtal) + 1024 bytes per chunk (64 chunks at most);
+ *   packed_host    host buffer that receives one packed stream per chunk of
+ *                  calorimeter-fills, back to back, in (fill, calo) order; each
+ *                  stream decodes on its own (daq_unpack_pool) into that
+ *                  chunk's pool rows, and the streams' rows concatenated are
+ *                  the call's pool rows (the records' pool_row index them);
+ *   packed_bytes_host  host int64, receives the total size of the streams.
  */
 typedef struct daq_host_io {
     const int16_t *samples_host;
@@ -225,6 +237,11 @@ typedef struct daq_host_io {
     int64_t pool_host_cap;
     int32_t *pedestal_host;
     int64_t *counts_host;
+    void *packed_dev;
+    int64_t packed_dev_cap;
+    uint8_t *packed_host;
+    int64_t packed_host_cap;
+    int64_t *packed_bytes_host;
 } daq_host_io;
 
 /*

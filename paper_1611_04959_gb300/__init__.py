@@ -20,7 +20,7 @@ LIB_PATH = _build.LIB
 # status codes and flags (include/daq.h)
 DAQ_OK, DAQ_EINVAL, DAQ_ECAPACITY, DAQ_ECUDA, DAQ_ETIMEOUT, DAQ_EUNSUPPORTED, DAQ_ESCRATCH = 0, -1, -2, -3, -4, -5, -6
 DAQ_STATIC_SCRATCH_BYTES = 8 << 20
-DAQ_SKIP_Q, DAQ_SKIP_ISLANDS, DAQ_SYNC = 1, 2, 4
+DAQ_SKIP_Q, DAQ_SKIP_ISLANDS, DAQ_SYNC, DAQ_PACK_POOL = 1, 2, 4, 8
 DAQ_DEV_HDR_OVERFLOW, DAQ_DEV_POOL_OVERFLOW, DAQ_DEV_TIMEOUT, DAQ_DEV_BAD_FILL_LEN = 1, 2, 4, 8
 
 ISLAND_DTYPE = np.dtype([("fill", "<i4"), ("calo", "<i4"), ("start", "<i4"), ("len", "<i4"),
@@ -45,7 +45,9 @@ class DaqIslands(ctypes.Structure):
 class DaqHostIO(ctypes.Structure):
     _fields_ = [("samples_host", ctypes.c_void_p), ("samples_dev", ctypes.c_void_p), ("hdr_host", ctypes.c_void_p),
                 ("hdr_host_cap", ctypes.c_int64), ("pool_host", ctypes.c_void_p), ("pool_host_cap", ctypes.c_int64),
-                ("pedestal_host", ctypes.c_void_p), ("counts_host", ctypes.c_void_p)]
+                ("pedestal_host", ctypes.c_void_p), ("counts_host", ctypes.c_void_p),
+                ("packed_dev", ctypes.c_void_p), ("packed_dev_cap", ctypes.c_int64), ("packed_host", ctypes.c_void_p),
+                ("packed_host_cap", ctypes.c_int64), ("packed_bytes_host", ctypes.c_void_p)]
 
 
 class DaqTuneResult(ctypes.Structure):

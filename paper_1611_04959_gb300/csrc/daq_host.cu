@@ -30,11 +30,15 @@ constexpr int kMaxDevices = 64;
 struct HostPipe {
     std::mutex call;  // one call at a time per device
     bool ready = false;
-    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaStream_t h2d = nullptr, d2h = nullptr, pk = nullptr;
     cudaEvent_t entry = nullptr;
-    cudaEvent_t in_ev[kMaxChunks] = {}, proc_ev[kMaxChunks] = {};
+    cudaEvent_t in_ev[kMaxChunks] = {}, proc_ev[kMaxChunks] = {}, pack_ev[kMaxChunks] = {};
     int64_t *counts_d = nullptr;  // [kMaxChunks][4] device
     int64_t *counts_h = nullptr;  // [kMaxChunks][4] page-locked
+    int64_t *psize_d = nullptr;   // [kMaxChunks] packed stream sizes, device
+    int64_t *psize_h = nullptr;   // [kMaxChunks] page-locked
+    void *pack_ws = nullptr;      // packing scratch, grown on demand
+    size_t pack_ws_bytes = 0;
 };
 
 std::mutex g_mu;
@@ -48,14 +52,18 @@ int pipe_for(int dev, HostPipe **out)
     if (!hp.ready) {
         if (cudaStreamCreateWithFlags(&hp.h2d, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&hp.d2h, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&hp.pk, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&hp.entry, cudaEventDisableTiming) != cudaSuccess)
             return DAQ_ECUDA;
         for (int j = 0; j < kMaxChunks; ++j)
             if (cudaEventCreateWithFlags(&hp.in_ev[j], cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&hp.proc_ev[j], cudaEventDisableTiming) != cudaSuccess)
+                cudaEventCreateWithFlags(&hp.proc_ev[j], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&hp.pack_ev[j], cudaEventDisableTiming) != cudaSuccess)
                 return DAQ_ECUDA;
         if (cudaMalloc(&hp.counts_d, sizeof(int64_t) * 4 * kMaxChunks) != cudaSuccess ||
-            cudaMallocHost(&hp.counts_h, sizeof(int64_t) * 4 * kMaxChunks) != cudaSuccess)
+            cudaMallocHost(&hp.counts_h, sizeof(int64_t) * 4 * kMaxChunks) != cudaSuccess ||
+            cudaMalloc(&hp.psize_d, sizeof(int64_t) * kMaxChunks) != cudaSuccess ||
+            cudaMallocHost(&hp.psize_h, sizeof(int64_t) * kMaxChunks) != cudaSuccess)
             return DAQ_ECUDA;
         hp.ready = true;
     }
@@ -67,6 +75,7 @@ struct Chunk {
     int f0, nf, c0, nc;
     int64_t hdr_off, hdr_cap, row_off, row_cap;  // device regions (records, rows)
     int64_t isl_at, isl_copied, rows_before;     // host placement
+    int64_t pk_off, pk_cap;                      // device region of the packed stream
 };
 
 // Chunks of about U / kTargetChunks calorimeter-fills, never splitting a
@@ -79,10 +88,10 @@ std::vector<Chunk> make_chunks(int F, int C)
     const int64_t u = (U + kTargetChunks - 1) / kTargetChunks;
     if (u >= C) {
         const int m = (int)(u / C);
-        for (int f = 0; f < F; f += m) v.push_back(Chunk{f, std::min(m, F - f), 0, C, 0, 0, 0, 0, 0, 0, 0});
+        for (int f = 0; f < F; f += m) v.push_back(Chunk{f, std::min(m, F - f), 0, C, 0, 0, 0, 0, 0, 0, 0, 0, 0});
     } else {
         for (int f = 0; f < F; ++f)
-            for (int c = 0; c < C; c += (int)u) v.push_back(Chunk{f, 1, c, std::min((int)u, C - c), 0, 0, 0, 0, 0, 0, 0});
+            for (int c = 0; c < C; c += (int)u) v.push_back(Chunk{f, 1, c, std::min((int)u, C - c), 0, 0, 0, 0, 0, 0, 0, 0, 0});
     }
     return v;
 }
@@ -104,6 +113,10 @@ extern "C" int daq_process_fills_host(int n_calo, int n_xtal, int64_t n_samples,
                       io->hdr_host_cap < 0 || io->pool_host_cap < 0))
         return DAQ_EINVAL;
     if (!dev->counts) return DAQ_EINVAL;
+    const bool pack = (params->flags & DAQ_PACK_POOL) != 0 && !skip_isl;
+    if (pack && (!io->packed_dev || io->packed_dev_cap < 0 || (reinterpret_cast<uintptr_t>(io->packed_dev) & 15) ||
+                 !io->packed_bytes_host || io->packed_host_cap < 0 || (io->packed_host_cap > 0 && !io->packed_host)))
+        return DAQ_EINVAL;
     // Validate the whole call (sizes, parameters, workspace) before any copy.
     size_t need = 0;
     int rc = daq_workspace_size(n_calo, n_xtal, n_samples, n_fills, params, &need);
@@ -121,7 +134,7 @@ extern "C" int daq_process_fills_host(int n_calo, int n_xtal, int64_t n_samples,
     // sample marked; an island per two samples), rows rounded to 8 so every
     // region starts 16-byte aligned.  Too little device capacity: one chunk.
     std::vector<Chunk> ch = make_chunks(n_fills, n_calo);
-    if (ch.empty()) ch.push_back(Chunk{0, n_fills, 0, n_calo, 0, 0, 0, 0, 0, 0, 0});
+    if (ch.empty()) ch.push_back(Chunk{0, n_fills, 0, n_calo, 0, 0, 0, 0, 0, 0, 0, 0, 0});
     {
         int64_t h = 0, r = 0;
         for (Chunk &c : ch) {
@@ -135,10 +148,30 @@ extern "C" int daq_process_fills_host(int n_calo, int n_xtal, int64_t n_samples,
         }
         if (ch.size() > 1 && !skip_isl && (h > dev->hdr_cap || r > dev->pool_row_cap)) ch.resize(1);
         if (ch.size() == 1) {
-            ch[0] = Chunk{0, n_fills, 0, n_calo, 0, dev->hdr_cap, 0, dev->pool_row_cap, 0, 0, 0};
+            ch[0] = Chunk{0, n_fills, 0, n_calo, 0, dev->hdr_cap, 0, dev->pool_row_cap, 0, 0, 0, 0, 0};
         }
     }
     const int nch = (int)ch.size();
+    if (pack) {
+        int64_t off = 0;
+        size_t ws_need = 0;
+        for (Chunk &c : ch) {
+            c.pk_off = off;
+            c.pk_cap = (daq_pack_bound(c.row_cap, n_xtal) + 15) & ~int64_t(15);
+            off += c.pk_cap;
+            size_t w = 0;
+            if (daq_pack_workspace_size(c.row_cap, n_xtal, &w) != DAQ_OK) return DAQ_EINVAL;
+            ws_need = std::max(ws_need, w);
+        }
+        if (off > io->packed_dev_cap) return DAQ_EINVAL;
+        if (ws_need > hp->pack_ws_bytes) {  // grown once per device and size
+            if (hp->pack_ws) cudaFree(hp->pack_ws);
+            hp->pack_ws = nullptr;
+            hp->pack_ws_bytes = 0;
+            if (cudaMalloc(&hp->pack_ws, ws_need) != cudaSuccess) return DAQ_ECUDA;
+            hp->pack_ws_bytes = ws_need;
+        }
+    }
 
     // Enqueue every copy-in and every chunk's processing up front.
     if (cudaEventRecord(hp->entry, s) != cudaSuccess || cudaStreamWaitEvent(hp->h2d, hp->entry, 0) != cudaSuccess)
@@ -159,7 +192,7 @@ extern "C" int daq_process_fills_host(int n_calo, int n_xtal, int64_t n_samples,
             break;
         }
         daq_params p = *params;
-        p.flags &= ~DAQ_SYNC;
+        p.flags &= ~(DAQ_SYNC | DAQ_PACK_POOL);
         p.events = nullptr;
         p.trace = nullptr;
         p.fill_base = params->fill_base + c.f0;
@@ -184,8 +217,23 @@ extern "C" int daq_process_fills_host(int n_calo, int n_xtal, int64_t n_samples,
         ++enq;
     }
 
-    // Copy each chunk's results back as soon as it is done.
-    int64_t tot_isl = 0, tot_rows = 0, tot_tiles = 0, bits = 0;
+    // Copy each chunk's results back as soon as it is done.  Packed form: the
+    // chunk's pool is packed on its own stream right away, and its stream
+    // (size read back with it) travels once the next chunk has been handed over.
+    int64_t tot_isl = 0, tot_rows = 0, tot_tiles = 0, bits = 0, packed_at = 0;
+    int pending = -1;  // chunk whose packed stream is still to be copied back
+    auto finish_pack = [&](int j) {
+        if (cudaEventSynchronize(hp->pack_ev[j]) != cudaSuccess) {
+            rc = DAQ_ECUDA;
+            return;
+        }
+        const int64_t n = hp->psize_h[j];
+        const int64_t k = std::max<int64_t>(0, std::min(n, io->packed_host_cap - packed_at));
+        if (k > 0 && cudaMemcpyAsync(io->packed_host + packed_at, static_cast<unsigned char *>(io->packed_dev) + ch[j].pk_off,
+                                     (size_t)k, cudaMemcpyDeviceToHost, hp->d2h) != cudaSuccess)
+            rc = DAQ_ECUDA;
+        packed_at += n;
+    };
     for (int j = 0; j < enq; ++j) {
         if (cudaEventSynchronize(hp->proc_ev[j]) != cudaSuccess) {
             rc = DAQ_ECUDA;
@@ -205,17 +253,32 @@ extern "C" int daq_process_fills_host(int n_calo, int n_xtal, int64_t n_samples,
             if (h > 0 && cudaMemcpyAsync(io->hdr_host + tot_isl, dev->hdr + c.hdr_off, (size_t)h * sizeof(daq_island),
                                          cudaMemcpyDeviceToHost, hp->d2h) != cudaSuccess)
                 rc = DAQ_ECUDA;
-            if (r > 0 && cudaMemcpyAsync(io->pool_host + tot_rows * X, dev->pool + c.row_off * X,
-                                         (size_t)(r * X) * sizeof(int16_t), cudaMemcpyDeviceToHost, hp->d2h) !=
-                             cudaSuccess)
+            if (pack) {
+                const int64_t rows_j = std::min(cnt[1], c.row_cap);
+                if (cudaStreamWaitEvent(hp->pk, hp->proc_ev[j], 0) != cudaSuccess ||
+                    daq_pack_pool(dev->pool + c.row_off * X, rows_j, n_xtal,
+                                  static_cast<unsigned char *>(io->packed_dev) + c.pk_off, c.pk_cap, hp->psize_d + j,
+                                  hp->pack_ws, hp->pack_ws_bytes, hp->pk) != DAQ_OK ||
+                    cudaMemcpyAsync(hp->psize_h + j, hp->psize_d + j, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                    hp->pk) != cudaSuccess ||
+                    cudaEventRecord(hp->pack_ev[j], hp->pk) != cudaSuccess)
+                    rc = DAQ_ECUDA;
+                if (rc == DAQ_OK && pending >= 0) finish_pack(pending);
+                pending = j;
+            } else if (r > 0 && cudaMemcpyAsync(io->pool_host + tot_rows * X, dev->pool + c.row_off * X,
+                                                (size_t)(r * X) * sizeof(int16_t), cudaMemcpyDeviceToHost, hp->d2h) !=
+                                    cudaSuccess) {
                 rc = DAQ_ECUDA;
+            }
         }
         tot_isl += cnt[0];
         tot_rows += cnt[1];
     }
-    if (enq < nch) {  // something failed while enqueueing: let the work in flight finish
+    if (rc == DAQ_OK && pending >= 0) finish_pack(pending);
+    if (enq < nch || rc != DAQ_OK) {  // something failed: let the work in flight finish
         cudaStreamSynchronize(hp->h2d);
         cudaStreamSynchronize(s);
+        cudaStreamSynchronize(hp->pk);
     }
     if (rc == DAQ_OK && !skip_isl && io->pedestal_host && dev->pedestal) {
         const size_t pb = (size_t)n_fills * C * X * sizeof(int32_t);
@@ -229,11 +292,14 @@ extern "C" int daq_process_fills_host(int n_calo, int n_xtal, int64_t n_samples,
     if (!skip_isl && nch > 1)
         for (const Chunk &c : ch)
             for (int64_t i = 0; i < c.isl_copied; ++i) io->hdr_host[c.isl_at + i].pool_row += c.rows_before;
+    if (pack) *io->packed_bytes_host = packed_at;
     io->counts_host[0] = tot_isl;
     io->counts_host[1] = tot_rows;
     io->counts_host[2] = bits;
     io->counts_host[3] = tot_tiles;
     rc = daq_status_from_counts(io->counts_host);
-    if (rc == DAQ_OK && !skip_isl && (tot_isl > io->hdr_host_cap || tot_rows > io->pool_host_cap)) rc = DAQ_ECAPACITY;
+    if (rc == DAQ_OK && !skip_isl &&
+        (tot_isl > io->hdr_host_cap || (pack ? packed_at > io->packed_host_cap : tot_rows > io->pool_host_cap)))
+        rc = DAQ_ECAPACITY;
     return rc;
 }

@@ -36,32 +36,30 @@ constexpr uint32_t kMagic = 0x50514144u;
 constexpr int kScanPer = 4;
 constexpr int kScanChunk = kThreads * kScanPer;
 
-// shared-memory row pitch (int16 elements): an odd number of 32-bit words
-__host__ __device__ __forceinline__ int row_pitch(int X) { return 2 * (((X + 1) / 2) | 1); }
-
 __device__ __forceinline__ uint32_t zigzag(int32_t d) { return d >= 0 ? 2u * (uint32_t)d : 2u * (uint32_t)(-d) - 1u; }
 
 __device__ __forceinline__ int32_t unzigzag(uint32_t z) { return (z & 1u) ? -(int32_t)((z + 1u) >> 1) : (int32_t)(z >> 1); }
 
-// Copy block b's rows into the warp's shared rows (padding rows past the end
-// with the final row).  Returns the number of real rows.
+// A warp's shared rows: the block's 32 rows back to back (row pitch X), as in
+// the pool.  Reading one crystal down the rows strides X int16 per lane, which
+// is conflict-free whenever X/2 is odd (54 crystals: 27 words per row).
+constexpr int kBlockElems = 32 * kMaxX;
+
+// Copy block b's rows (16-byte vectors; the pool and every block start are
+// 16-byte aligned) into the warp's shared rows, rows past the pool's end
+// repeating its final row.  Returns the number of real rows.
 __device__ __forceinline__ int load_block(const int16_t *pool, long long rows, int X, long long b, int16_t *sm,
                                           int lane)
 {
     const long long r0 = 32ll * b;
     const int nv = (int)min(32ll, rows - r0);
-    const int P = row_pitch(X);
+    const int n = nv * X;  // int16 elements
     const int16_t *src = pool + r0 * X;
-    const int n = nv * X;
-    for (int e = lane; e < n; e += 32) {
-        const int i = e / X, x = e - i * X;
-        sm[i * P + x] = src[e];
-    }
+    const int nvec = n >> 3;
+    for (int k = lane; k < nvec; k += 32) reinterpret_cast<int4 *>(sm)[k] = reinterpret_cast<const int4 *>(src)[k];
+    for (int e = (nvec << 3) + lane; e < n; e += 32) sm[e] = src[e];
     __syncwarp();
-    for (int e = lane; e < (32 - nv) * X; e += 32) {
-        const int i = nv + e / X, x = e % X;
-        sm[i * P + x] = sm[(nv - 1) * P + x];
-    }
+    for (int e = n + lane; e < 32 * X; e += 32) sm[e] = sm[(nv - 1) * X + (e - n) % X];
     __syncwarp();
     return nv;
 }
@@ -69,10 +67,10 @@ __device__ __forceinline__ int load_block(const int16_t *pool, long long rows, i
 __global__ void __launch_bounds__(kThreads) pack_size_kernel(const int16_t *pool, long long rows, int X,
                                                              long long nb, unsigned long long *sizes)
 {
-    __shared__ int16_t sm_all[kWarps][32 * 2 * ((kMaxX / 2) | 1)];
+    __shared__ __align__(16) int16_t sm_all[kWarps][kBlockElems];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int16_t *sm = sm_all[warp];
-    const int P = row_pitch(X);
+    const int P = X;
     for (long long b = (long long)blockIdx.x * kWarps + warp; b < nb; b += (long long)gridDim.x * kWarps) {
         load_block(pool, rows, X, b, sm, lane);
         unsigned words = 0;
@@ -179,10 +177,10 @@ __global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *poo
                                                               const unsigned long long *offs, unsigned char *out,
                                                               long long cap)
 {
-    __shared__ int16_t sm_all[kWarps][32 * 2 * ((kMaxX / 2) | 1)];
+    __shared__ __align__(16) int16_t sm_all[kWarps][kBlockElems];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int16_t *sm = sm_all[warp];
-    const int P = row_pitch(X);
+    const int P = X;
     const long long head = 16 + 8 * (nb + 1);
     if (blockIdx.x == 0 && threadIdx.x == 0 && cap >= 16) {
         uint32_t *h = reinterpret_cast<uint32_t *>(out);
@@ -216,10 +214,10 @@ __global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *poo
 __global__ void __launch_bounds__(kThreads) unpack_kernel(const unsigned char *in, long long in_bytes, long long rows,
                                                           int X, long long nb, int16_t *pool_out, int *err)
 {
-    __shared__ int16_t sm_all[kWarps][32 * 2 * ((kMaxX / 2) | 1)];
+    __shared__ __align__(16) int16_t sm_all[kWarps][kBlockElems];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int16_t *sm = sm_all[warp];
-    const int P = row_pitch(X);
+    const int P = X;
     const long long head = 16 + 8 * (nb + 1);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const uint32_t *h = reinterpret_cast<const uint32_t *>(in);
@@ -268,10 +266,14 @@ __global__ void __launch_bounds__(kThreads) unpack_kernel(const unsigned char *i
         const long long r0 = 32ll * b;
         const int nv = (int)min(32ll, rows - r0);
         int16_t *dst = pool_out + r0 * X;
-        for (int e = lane; e < nv * X; e += 32) {
-            const int i = e / X, x = e - i * X;
-            dst[e] = sm[i * P + x];
+        const int n = nv * X;
+        int done = 0;
+        if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {  // 16-byte vectors where the output allows
+            const int nvec = n >> 3;
+            for (int k = lane; k < nvec; k += 32) reinterpret_cast<int4 *>(dst)[k] = reinterpret_cast<const int4 *>(sm)[k];
+            done = nvec << 3;
         }
+        for (int e = done + lane; e < n; e += 32) dst[e] = sm[e];
         __syncwarp();
     }
 }

@@ -24,7 +24,23 @@ def env():
     return dict(torch=torch, oracle=oracle, synth=synth, daq=daq)
 
 
-def run_host(env, s, params, fill_len=None, dev_rows=None, dev_hdr=None, host_rows=None, q=None):
+def split_streams(buf: np.ndarray, total: int) -> list:
+    """The back-to-back packed streams of the host form: (stream bytes, rows, n_xtal)."""
+    out, at = [], 0
+    while at < total:
+        head = buf[at: at + 16]
+        X = int(head[4:8].view("<u4")[0])
+        rows = int(head[8:16].view("<u8")[0])
+        nb = -(-rows // 32)
+        payload = int(buf[at + 16 + 8 * nb: at + 24 + 8 * nb].view("<u8")[0])
+        size = 16 + 8 * (nb + 1) + payload
+        out.append((buf[at: at + size], rows, X))
+        at += size
+    assert at == total
+    return out
+
+
+def run_host(env, s, params, fill_len=None, dev_rows=None, dev_hdr=None, host_rows=None, q=None, pack=False):
     torch, daq = env["torch"], env["daq"]
     F, C, X, N = s.shape
     host = torch.from_numpy(s).pin_memory()
@@ -46,7 +62,19 @@ def run_host(env, s, params, fill_len=None, dev_rows=None, dev_hdr=None, host_ro
     p.workspace, p.workspace_bytes = ws.data_ptr(), ws.numel()
     io = daq.DaqHostIO(host.data_ptr(), sdev.data_ptr(), hdr_h.ctypes.data, len(hdr_h), pool_h.data_ptr(), hrows,
                        ped_h.ctypes.data, counts_h.ctypes.data)
+    if pack:
+        p.flags |= daq.DAQ_PACK_POOL
+        cap = daq.daq_pack_bound(F * C * N, X) + 64 * 8192
+        pdev = torch.empty(cap, dtype=torch.uint8, device="cuda")
+        phost = np.zeros(cap, np.uint8)
+        pbytes = np.zeros(1, np.int64)
+        io.packed_dev, io.packed_dev_cap = pdev.data_ptr(), cap
+        io.packed_host, io.packed_host_cap, io.packed_bytes_host = phost.ctypes.data, cap, pbytes.ctypes.data
     rc = daq.daq_process_fills_host(C, X, N, F, p, out.struct(), q.data_ptr(), io)
+    if pack:
+        pool = [env["oracle"].unpack(st, rows, xx) for st, rows, xx in split_streams(phost, int(pbytes[0]))]
+        pool = np.concatenate(pool) if pool else np.zeros((0, X), np.int16)
+        return rc, counts_h, hdr_h, pool, ped_h, q
     return rc, counts_h, hdr_h, pool_h.numpy(), ped_h, q
 
 
@@ -122,3 +150,12 @@ def test_calorimeter_groups_write_true_indices_and_q_rows(env):
     assert np.array_equal(np.concatenate(isl), ref["islands"])
     assert np.array_equal(np.concatenate(pools), ref["pool"])
     assert np.array_equal(q.cpu().numpy(), ref["q"])
+
+
+@pytest.mark.parametrize("F,C,N", [(1, 24, 20_000), (3, 2, 16_000), (1, 1, 50_000)])
+def test_packed_host_form_matches_oracle(env, F, C, N):
+    from synth import workloads as W
+    w = W.scaled(W.PLAIN_FULL_FILL, n_fills=F, n_calo=C, n_samples=N)
+    s = env["synth"].generate(w.config())
+    ref = env["oracle"].process_fills(s, w.params(), n_threads=8)
+    check(run_host(env, s, w.params(), pack=True), ref)
