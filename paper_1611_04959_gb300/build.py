@@ -35,20 +35,43 @@ def nvcc() -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ into one shared library (one -gencode, -lineinfo)."""
+    """Compile every .cu under csrc/ (in parallel, one -gencode, -lineinfo) and
+    link them into one shared library."""
     if not force and not stale():
         return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), "-O3", "-lineinfo", "-std=c++17", *ARCH, "-shared", "-Xcompiler", "-fPIC",
-           "-I" + INCLUDE, "-I" + CSRC, "-o", tmp, *sources()]
+    import concurrent.futures as cf
+    obj_dir = os.path.join(PKG, "_build")
+    os.makedirs(obj_dir, exist_ok=True)
+    base = [nvcc(), "-O3", "-lineinfo", "-std=c++17", *ARCH, "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    r = subprocess.run(cmd, capture_output=True, text=True)
+        base.insert(1, "-Xptxas=-v")
+
+    def compile_one(src: str):
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + f".{os.getpid()}.o")
+        r = subprocess.run(base + ["-c", "-o", obj, src], capture_output=True, text=True)
+        return src, obj, r
+
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        results = list(ex.map(compile_one, sources()))
+    failed = [(src, r) for src, _, r in results if r.returncode != 0]
+    if verbose:
+        for _, _, r in results:
+            sys.stderr.write(r.stderr)
+    if failed:
+        for src, r in failed:
+            sys.stderr.write(f"--- {src}\n" + r.stdout + r.stderr)
+        raise RuntimeError("nvcc failed building libdaq.so")
+    tmp = LIB + f".tmp{os.getpid()}"
+    r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *[o for _, o, _ in results]], capture_output=True,
+                       text=True)
+    for _, o, _ in results:
+        try:
+            os.remove(o)
+        except OSError:
+            pass
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)
-        raise RuntimeError("nvcc failed building libdaq.so")
-    if verbose:
-        sys.stderr.write(r.stderr)
+        raise RuntimeError("nvcc failed linking libdaq.so")
     os.replace(tmp, LIB)
     return LIB
 
