@@ -175,6 +175,24 @@ __device__ __forceinline__ void tma_load_2d_hint(void *dst, const void *tmap, in
         : "memory");
 }
 
+// L2 prefetch of one 2-D tensor box (no shared memory, no completion); the
+// box must lie inside the tensor.
+__device__ __forceinline__ void tma_prefetch_2d(const void *tmap, int c0, int c1)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                     reinterpret_cast<uint64_t>(tmap)),
+                 "r"(c0), "r"(c1)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch_2d_hint(const void *tmap, int c0, int c1, uint64_t policy)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile.L2::cache_hint [%0, {%1, %2}], %3;" ::"l"(
+                     reinterpret_cast<uint64_t>(tmap)),
+                 "r"(c0), "r"(c1), "l"(policy)
+                 : "memory");
+}
+
 __device__ __forceinline__ void ld_relaxed_b128(const void *p, unsigned long long &lo, unsigned long long &hi)
 {
     asm volatile(

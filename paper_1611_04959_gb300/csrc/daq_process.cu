@@ -37,6 +37,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -44,6 +45,7 @@
 #include "daq_device.cuh"
 #include "daq_steps.cuh"
 #include "daq_twopass.cuh"
+#include "daq_stream.cuh"
 
 namespace daq {
 
@@ -616,6 +618,15 @@ static size_t plain_smem_bytes(int tw, int X, int slot_bytes, int rs, int need_s
     return (b + 127) & ~size_t(127);
 }
 
+static size_t stream_smem(int tw, int X, int slot_bytes_b, int need_sarr)
+{
+    switch (tw) {
+    case 128: return StreamSmem<128>(X, slot_bytes_b, need_sarr).total;
+    case 224: return StreamSmem<224>(X, slot_bytes_b, need_sarr).total;
+    default: return StreamSmem<448>(X, slot_bytes_b, need_sarr).total;
+    }
+}
+
 static size_t pipe_smem(int tw, int X, int slot_bytes, int rs, int need_sarr)
 {
     switch (tw) {
@@ -702,7 +713,9 @@ static void plan_geometry(Plan *pl, int tw, int pre, int post, int X)
     pl->rs_b = 2 * pl->boxw_b;
     pl->slot_bytes_b = pl->nbox_b * pl->box_stride_b;
     pl->smem_b = 0;
-    if (pl->mode == kModePipelined) {
+    if (pl->mode == kModeStream) {
+        pl->smem = stream_smem(tw, X, pl->slot_bytes_b, pl->need_sarr);
+    } else if (pl->mode == kModePipelined) {
         pl->smem = pipe_smem(tw, X, pl->slot_bytes, pl->rs, pl->need_sarr);
     } else if (pl->mode == kModePlain) {
         pl->smem = plain_smem_bytes(tw, X, pl->slot_bytes, pl->rs, pl->need_sarr);
@@ -753,7 +766,7 @@ static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, con
     if (n_xtal > kMaxXtal) return DAQ_EUNSUPPORTED;
     if (p->pre < 0 || p->post < 0 || p->pre + p->post > 512 || p->ped_samples < 1) return DAQ_EINVAL;
     if (p->n_decim < 0 || p->n_decim > 2) return DAQ_EINVAL;
-    if (p->grid < -4) return DAQ_EINVAL;
+    if (p->grid < -5) return DAQ_EINVAL;
     if (p->lag_tiles < 0) return DAQ_EINVAL;
     if (p->calo_base < 0 || p->q_calos < 0 ||
         (int64_t)p->calo_base + n_calo > (p->q_calos > 0 ? (int64_t)p->q_calos : (int64_t)n_calo))
@@ -767,8 +780,11 @@ static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, con
         if (p->decim[d] % 8) pl->need_sarr = 1;
     }
     if (p->tile != 0 && p->tile != 128 && p->tile != 224 && p->tile != 448 && p->tile != 960) return DAQ_EINVAL;
-    pl->mode = p->grid >= 0 ? kModeTwoPass
-                            : (p->grid == -3 ? kModePipelined : (p->grid == -4 ? kModeFused : kModePlain));
+    pl->mode = p->grid >= 0    ? kModeTwoPass
+               : p->grid == -3 ? kModePipelined
+               : p->grid == -4 ? kModeFused
+               : p->grid == -5 ? kModeStream
+                               : kModePlain;
     const int hl = (p->post + 1 + 7) & ~7, hr = (p->pre + 1 + 7) & ~7;
     const int limit = p->tile ? p->tile : 448;
     int chosen = -1;
@@ -866,6 +882,17 @@ static cudaError_t launch_twopass(const KArgs &a, const Plan &pl, int grid, int 
     }
     if (ev && (e = cudaEventRecord(ev[4], s)) != cudaSuccess) return e;
     return cudaSuccess;
+}
+
+// Streaming single-pass form: one persistent CTA per SM (at most one per tile).
+template <int TW> static cudaError_t launch_stream(const KArgs &a, const Plan &pl, int sms, cudaStream_t s)
+{
+    static size_t conf[64] = {0};
+    cudaError_t e = ensure_smem(daq_stream_kernel<TW>, pl.smem, conf);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, pl.max_tiles));
+    daq_stream_kernel<TW><<<grid, kStrThreads, pl.smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 // Single-launch form: one cooperative launch of every CTA that fits (roles by
@@ -996,9 +1023,43 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
                                       n_xtal) &&
                     encode_tensor_map(&a.tmap_b, samples, (int64_t)n_fills * n_calo * n_xtal, n_samples,
                                       pl.boxw_b, n_xtal);
+    if (pl.mode == kModeStream && !a.use_tma) {
+        // the streaming form reads 16-byte groups and bulk-copies tiles: rows
+        // that are not 16-byte aligned take the two-pass form
+        daq_params q = p;
+        q.grid = 0;
+        rc = make_plan(n_calo, n_xtal, n_samples, n_fills, &q, &pl);
+        if (rc) return rc;
+        a.hl = pl.hl;
+        a.hr = pl.hr;
+        a.ew = pl.ew;
+        a.rs = pl.rs;
+        a.boxw = pl.boxw;
+        a.nbox = pl.nbox;
+        a.box_stride = pl.box_stride;
+        a.slot_bytes = pl.slot_bytes;
+        a.boxw_b = pl.boxw_b;
+        a.nbox_b = pl.nbox_b;
+        a.box_stride_b = pl.box_stride_b;
+        a.slot_bytes_b = pl.slot_bytes_b;
+        a.rs_b = pl.rs_b;
+        a.mode = pl.mode;
+        if (total > 0 && n_samples % 8 == 0 && (reinterpret_cast<uintptr_t>(samples) & 15) == 0)
+            a.use_tma = encode_tensor_map(&a.tmap, samples, (int64_t)n_fills * n_calo * n_xtal, n_samples, pl.boxw,
+                                          n_xtal) &&
+                        encode_tensor_map(&a.tmap_b, samples, (int64_t)n_fills * n_calo * n_xtal, n_samples,
+                                          pl.boxw_b, n_xtal);
+    }
     a.need_sarr = pl.need_sarr;
     a.max_tiles = pl.max_tiles;
     a.lag_tiles = std::max<int64_t>(p.lag_tiles > 0 ? p.lag_tiles : kFusedLagTiles, kFusedMinLag);
+    {
+        static const int pf_env = [] {
+            const char *e = std::getenv("DAQ_PF");
+            return e ? std::atoi(e) : 0;
+        }();
+        a.pf_dist = pf_env;
+    }
     a.hdr = skip_isl ? nullptr : out->hdr;
     a.hdr_cap = skip_isl ? 0 : out->hdr_cap;
     a.pool = skip_isl ? nullptr : out->pool;
@@ -1036,7 +1097,13 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
 
     const int64_t tiles_cap = std::max<int64_t>(1, std::min<int64_t>(pl.max_tiles, INT32_MAX));
     cudaError_t e;
-    if (pl.mode == kModeFused) {
+    if (pl.mode == kModeStream) {
+        switch (pl.tw) {
+        case 128: e = launch_stream<128>(a, pl, di.sms, s); break;
+        case 224: e = launch_stream<224>(a, pl, di.sms, s); break;
+        default: e = launch_stream<448>(a, pl, di.sms, s); break;
+        }
+    } else if (pl.mode == kModeFused) {
         switch (pl.tw) {
         case 128: e = launch_fused<128>(a, pl, di.sms, ev, s); break;
         case 224: e = launch_fused<224>(a, pl, di.sms, ev, s); break;

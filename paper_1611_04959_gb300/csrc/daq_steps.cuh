@@ -22,7 +22,7 @@ namespace daq {
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // bounded device waits (4 s)
 constexpr int kMaxTileWords = 14;                 // marks words of the widest two-pass tile (448 samples)
 // kernels a call may use (daq_params.grid picks one)
-enum : int32_t { kModeTwoPass = 0, kModePlain = 1, kModePipelined = 2, kModeFused = 3 };
+enum : int32_t { kModeTwoPass = 0, kModePlain = 1, kModePipelined = 2, kModeFused = 3, kModeStream = 4 };
 constexpr int kMaxXtal = 64;
 constexpr int kMaxExtBits = 1024;  // tile + halos: one warp of 32-bit words
 
@@ -120,6 +120,7 @@ struct KArgs {
     // single-launch form: tiles the count role may run ahead of the compact
     // role, and the two progress counters (tiles scanned, tiles compacted)
     int64_t lag_tiles;
+    int32_t pf_dist;  // count pass: L2 prefetch of the CTA's tile pf_dist tiles after the one loaded (0 = none)
     unsigned long long *fctr;
     // outputs
     daq_island *hdr;
@@ -224,6 +225,21 @@ __device__ __forceinline__ void issue_tile_load(const KArgs &a, const TileInfo &
         return;
     }
     for (int k = 0; k < a.nbox; ++k) tma_load_2d(slot + (size_t)k * a.box_stride, &a.tmap, c0 + k * a.boxw, c1, bar);
+}
+
+// L2 prefetch of the boxes of one tile that lie wholly inside the tensor (one
+// thread).  A hint only: the tile's own load later reads these lines from L2.
+__device__ __forceinline__ void issue_tile_prefetch(const KArgs &a, const TileInfo &T)
+{
+    const int c0 = (int)(T.t0 - a.hl);
+    const int c1 = (int)(((long long)T.f * a.n_calo + T.c) * a.n_xtal);
+    const uint64_t pol = l2_policy_evict_last();
+    for (int k = 0; k < a.nbox; ++k) {
+        const long long col = (long long)c0 + (long long)k * a.boxw;
+        if (col < 0 || col + a.boxw > a.n_samples) continue;
+        if (a.mode == kModeFused || a.mode == kModeStream) tma_prefetch_2d_hint(&a.tmap, (int)col, c1, pol);
+        else tma_prefetch_2d(&a.tmap, (int)col, c1);
+    }
 }
 
 __device__ __forceinline__ uint32_t tile_load_bytes(const KArgs &a)

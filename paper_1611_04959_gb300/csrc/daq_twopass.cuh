@@ -187,6 +187,11 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(full + s, tile_load_bytes(a));
             issue_tile_load(a, T, slot0 + (size_t)s * a.slot_bytes, full + s);
+            if (a.pf_dist > 0) {
+                TileInfo P;
+                if (decode_tile<TW>(a, tile + (long long)a.pf_dist * G, P, plan.fts, plan.lens))
+                    issue_tile_prefetch(a, P);
+            }
         }
         trace_stamp(a, tile, 1);
     };
@@ -434,7 +439,7 @@ __device__ __forceinline__ void issue_tile_load_b(const KArgs &a, const TileInfo
 {
     const int c0 = (int)T.t0;
     const int c1 = (int)(((long long)T.f * a.n_calo + T.c) * a.n_xtal);
-    if (a.mode == kModeFused) {  // last use of these lines
+    if (a.mode == kModeFused || a.mode == kModeStream) {  // last use of these lines
         const uint64_t pol = l2_policy_evict_first();
         for (int k = 0; k < a.nbox_b; ++k)
             tma_load_2d_hint(slot + (size_t)k * a.box_stride_b, &a.tmap_b, c0 + k * a.boxw_b, c1, bar, pol);

@@ -50,7 +50,7 @@ def test_plain_one_calorimeter_full_fill(env):
 
 
 @pytest.mark.parametrize("tile", [128, 224, 448, 960])
-@pytest.mark.parametrize("grid", [0, -1, -2, -3, -4, 1, 5])
+@pytest.mark.parametrize("grid", [0, -1, -2, -3, -4, -5, 1, 5])
 def test_tile_and_grid_invariance(env, tile, grid):
     from synth import workloads as W
     w = W.scaled(W.PLAIN_FULL_FILL, n_calo=3, n_samples=40_000)
@@ -92,7 +92,7 @@ def test_random_shapes(env, seed):
     hr = (params["pre"] + 8) // 8 * 8
     if tile and tile + hl + hr > 1024:
         tile = 0
-    compare(env, s, params, fill_len=fill_len, tile=tile, grid=int(rng.choice([0, 0, -1, -2, -3, -4, -4, 2])))
+    compare(env, s, params, fill_len=fill_len, tile=tile, grid=int(rng.choice([0, 0, -1, -2, -3, -4, -4, 2, -5, -5])))
 
 
 def test_uneven_batch_of_fills(env):
@@ -175,9 +175,9 @@ def test_fill_length_out_of_range_is_flagged(env):
     assert e.value.status == daq.DAQ_EINVAL
 
 
-@pytest.mark.parametrize("grid", [0, -4])
+@pytest.mark.parametrize("grid", [0, -4, -5])
 def test_full_fill_24_calorimeters(env, grid):
-    """The benchmark workload itself (1.45 GB), full parity, both default forms."""
+    """The benchmark workload itself (1.45 GB), full parity: two-pass, single-launch and streaming forms."""
     from synth import workloads as W
     w = W.PLAIN_FULL_FILL
     s = env["synth"].generate(w.config())
