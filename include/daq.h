@@ -96,7 +96,12 @@ typedef struct daq_island {
  *                -3 = single-pass pipelined kernel (one CTA per SM, warp roles);
  *                -4 = single-launch form: the two passes in one cooperative
  *                     launch, the compact role a bounded distance behind the
- *                     count role so that its re-read hits L2.
+ *                     count role so that its re-read hits L2;
+ *                -5 = streaming single pass: one CTA per SM whose warps count
+ *                     tiles, look back over earlier tiles' states and compact
+ *                     each tile from L2 once its prefix is known (rows must be
+ *                     16-byte aligned with n_samples % 8 == 0, else the call
+ *                     takes the two-pass form).
  *   stream       cudaStream_t (NULL = legacy default stream).
  *   workspace    device scratch of at least daq_workspace_size() bytes,
  *                16-byte aligned; reused by the call and not to be shared by
@@ -570,6 +575,10 @@ int daq_status_from_counts(const int64_t *counts_host);
 
 /* Static, human-readable text for a daq_status. */
 const char *daq_strerror(int status);
+
+/* Name and text of the CUDA error behind the calling thread's last DAQ_ECUDA
+ * from daq_process_fills (static storage; "no error" when there was none). */
+const char *daq_last_cuda_error(void);
 
 /* ABI version (major * 100 + minor). */
 int daq_version(void);

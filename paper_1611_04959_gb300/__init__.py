@@ -95,7 +95,10 @@ class DaqServingSummary(ctypes.Structure):
 class DaqError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
-        super().__init__(f"{what}: {strerror(status)} ({status})" if what else f"{strerror(status)} ({status})")
+        msg = f"{what}: {strerror(status)} ({status})" if what else f"{strerror(status)} ({status})"
+        if status == DAQ_ECUDA:
+            msg += " [" + lib().daq_last_cuda_error().decode() + "]"
+        super().__init__(msg)
 
 
 _lock = threading.Lock()
@@ -133,6 +136,8 @@ def lib():
             L.daq_status_from_counts.restype = i32
             L.daq_strerror.argtypes = [i32]
             L.daq_strerror.restype = ctypes.c_char_p
+            L.daq_last_cuda_error.argtypes = []
+            L.daq_last_cuda_error.restype = ctypes.c_char_p
             L.daq_version.argtypes = []
             L.daq_version.restype = i32
             L.daq_batch_plan_create.argtypes = [vp, i32, i32, i64, i32, ctypes.POINTER(DaqParams),

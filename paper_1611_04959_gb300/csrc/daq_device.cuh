@@ -175,24 +175,6 @@ __device__ __forceinline__ void tma_load_2d_hint(void *dst, const void *tmap, in
         : "memory");
 }
 
-// L2 prefetch of one 2-D tensor box (no shared memory, no completion); the
-// box must lie inside the tensor.
-__device__ __forceinline__ void tma_prefetch_2d(const void *tmap, int c0, int c1)
-{
-    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
-                     reinterpret_cast<uint64_t>(tmap)),
-                 "r"(c0), "r"(c1)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tma_prefetch_2d_hint(const void *tmap, int c0, int c1, uint64_t policy)
-{
-    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile.L2::cache_hint [%0, {%1, %2}], %3;" ::"l"(
-                     reinterpret_cast<uint64_t>(tmap)),
-                 "r"(c0), "r"(c1), "l"(policy)
-                 : "memory");
-}
-
 __device__ __forceinline__ void ld_relaxed_b128(const void *p, unsigned long long &lo, unsigned long long &hi)
 {
     asm volatile(
@@ -215,6 +197,15 @@ __device__ __forceinline__ void ld_acquire_b128(const void *p, unsigned long lon
 __device__ __forceinline__ void st_release_b128(void *p, unsigned long long lo, unsigned long long hi)
 {
     asm volatile("{\n\t.reg .b128 t;\n\tmov.b128 t, {%0, %1};\n\tst.release.gpu.global.b128 [%2], t;\n\t}" ::"l"(lo),
+                 "l"(hi), "l"(p)
+                 : "memory");
+}
+
+// Relaxed 128-bit store: the 16 bytes are one single-copy-atomic access, with
+// no ordering of the thread's earlier accesses (for self-contained messages).
+__device__ __forceinline__ void st_relaxed_b128(void *p, unsigned long long lo, unsigned long long hi)
+{
+    asm volatile("{\n\t.reg .b128 t;\n\tmov.b128 t, {%0, %1};\n\tst.relaxed.gpu.global.b128 [%2], t;\n\t}" ::"l"(lo),
                  "l"(hi), "l"(p)
                  : "memory");
 }

@@ -37,6 +37,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -618,12 +619,12 @@ static size_t plain_smem_bytes(int tw, int X, int slot_bytes, int rs, int need_s
     return (b + 127) & ~size_t(127);
 }
 
-static size_t stream_smem(int tw, int X, int slot_bytes_b, int need_sarr)
+static size_t stream_smem(int tw, int X, int slot_bytes, int need_sarr, int nm, int ns)
 {
     switch (tw) {
-    case 128: return StreamSmem<128>(X, slot_bytes_b, need_sarr).total;
-    case 224: return StreamSmem<224>(X, slot_bytes_b, need_sarr).total;
-    default: return StreamSmem<448>(X, slot_bytes_b, need_sarr).total;
+    case 128: return StreamSmem<128>(X, slot_bytes, need_sarr, nm, ns).total;
+    case 224: return StreamSmem<224>(X, slot_bytes, need_sarr, nm, ns).total;
+    default: return StreamSmem<448>(X, slot_bytes, need_sarr, nm, ns).total;
     }
 }
 
@@ -668,6 +669,7 @@ struct Plan {
     int tw, hl, hr, ew, rs, boxw, nbox, box_stride, slot_bytes, need_sarr, mode;
     int boxw_b, nbox_b, box_stride_b, slot_bytes_b, rs_b;  // compact pass (two-pass mode)
     size_t smem, smem_b;                                   // tile (or count) kernel, compact kernel
+    int str_meta, str_stages;                              // streaming form: tile records, row stages per CTA
     int64_t max_tiles;
 };
 
@@ -714,7 +716,20 @@ static void plan_geometry(Plan *pl, int tw, int pre, int post, int X)
     pl->slot_bytes_b = pl->nbox_b * pl->box_stride_b;
     pl->smem_b = 0;
     if (pl->mode == kModeStream) {
-        pl->smem = stream_smem(tw, X, pl->slot_bytes_b, pl->need_sarr);
+        // two row stages if they fit, then as many tile records as fit (a
+        // multiple of 4: four look-back warps take turns)
+        const size_t budget = (size_t)kSmemBudget - 1024;  // static shared memory of the kernel
+        pl->str_stages = kStrMaxStages;
+        pl->str_meta = kStrMaxMeta;
+        for (;;) {
+            if (stream_smem(tw, X, pl->slot_bytes, pl->need_sarr, pl->str_meta, pl->str_stages) <= budget) break;
+            if (pl->str_meta > 4) pl->str_meta -= 4;
+            else if (pl->str_stages > 1) {
+                pl->str_stages -= 1;
+                pl->str_meta = kStrMaxMeta;
+            } else break;  // does not fit: make_plan tries a narrower tile
+        }
+        pl->smem = stream_smem(tw, X, pl->slot_bytes, pl->need_sarr, pl->str_meta, pl->str_stages);
     } else if (pl->mode == kModePipelined) {
         pl->smem = pipe_smem(tw, X, pl->slot_bytes, pl->rs, pl->need_sarr);
     } else if (pl->mode == kModePlain) {
@@ -919,6 +934,14 @@ static cudaError_t launch_fused(const KArgs &a, const Plan &pl, int sms, cudaEve
 
 static int64_t q_bins(int64_t n, int32_t d) { return d > 0 ? (n + d - 1) / d : 0; }
 
+// CUDA error behind this thread's last DAQ_ECUDA from daq_process_fills.
+static thread_local cudaError_t t_last_cuda = cudaSuccess;
+static int cuda_fail(cudaError_t e)
+{
+    t_last_cuda = e;
+    return DAQ_ECUDA;
+}
+
 }  // namespace daq
 
 using namespace daq;
@@ -1023,6 +1046,16 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
                                       n_xtal) &&
                     encode_tensor_map(&a.tmap_b, samples, (int64_t)n_fills * n_calo * n_xtal, n_samples,
                                       pl.boxw_b, n_xtal);
+    if (pl.mode == kModeStream && a.use_tma) {
+        PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+        cuuint64_t dims[2] = {(cuuint64_t)n_samples, (cuuint64_t)((int64_t)n_fills * n_calo * n_xtal)};
+        cuuint64_t strides[1] = {(cuuint64_t)n_samples * sizeof(int16_t)};
+        cuuint32_t box[2] = {(cuuint32_t)kStrStep, (cuuint32_t)n_xtal};
+        cuuint32_t estr[2] = {1, 1};
+        a.use_tma = enc && enc(&a.tmap_c, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<int16_t *>(samples), dims,
+                               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
     if (pl.mode == kModeStream && !a.use_tma) {
         // the streaming form reads 16-byte groups and bulk-copies tiles: rows
         // that are not 16-byte aligned take the two-pass form
@@ -1053,13 +1086,8 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
     a.need_sarr = pl.need_sarr;
     a.max_tiles = pl.max_tiles;
     a.lag_tiles = std::max<int64_t>(p.lag_tiles > 0 ? p.lag_tiles : kFusedLagTiles, kFusedMinLag);
-    {
-        static const int pf_env = [] {
-            const char *e = std::getenv("DAQ_PF");
-            return e ? std::atoi(e) : 0;
-        }();
-        a.pf_dist = pf_env;
-    }
+    a.str_meta = pl.str_meta;
+    a.str_stages = pl.str_stages;
     a.hdr = skip_isl ? nullptr : out->hdr;
     a.hdr_cap = skip_isl ? 0 : out->hdr_cap;
     a.pool = skip_isl ? nullptr : out->pool;
@@ -1092,7 +1120,7 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
     const long long n_cf = (long long)n_fills * n_calo;
     const int prep_grid = (int)std::max<long long>(1, std::min<long long>(std::max<long long>(n_cf, 1), 4ll * di.sms));
     daq_prepare_kernel<<<prep_grid, kThreads, 0, s>>>(a, pl.tw);
-    if (cudaGetLastError() != cudaSuccess) return DAQ_ECUDA;
+    if (cudaError_t e0 = cudaGetLastError()) return cuda_fail(e0);
     if (ev && cudaEventRecord(ev[1], s) != cudaSuccess) return DAQ_ECUDA;
 
     const int64_t tiles_cap = std::max<int64_t>(1, std::min<int64_t>(pl.max_tiles, INT32_MAX));
@@ -1133,7 +1161,7 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
         default: e = launch_plain<960>(a, pl, grid, s); break;
         }
     }
-    if (e != cudaSuccess) return DAQ_ECUDA;
+    if (e != cudaSuccess) return cuda_fail(e);
     if (ev && pl.mode != kModeTwoPass)
         for (int k = 2; k < 5; ++k)
             if (cudaEventRecord(ev[k], s) != cudaSuccess) return DAQ_ECUDA;
@@ -1178,5 +1206,12 @@ const char *daq_strerror(int status)
 }
 
 int daq_version(void) { return 101; }
+
+const char *daq_last_cuda_error(void)
+{
+    static thread_local char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s: %s", cudaGetErrorName(t_last_cuda), cudaGetErrorString(t_last_cuda));
+    return buf;
+}
 
 }  // extern "C"

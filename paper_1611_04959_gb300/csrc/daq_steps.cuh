@@ -96,6 +96,7 @@ __device__ __forceinline__ Agg shfl_down_agg(const Agg &a, int d)
 struct KArgs {
     CUtensorMap tmap;    // samples as a 2-D tensor [F*C*X rows][n_samples], when use_tma: boxes with halo
     CUtensorMap tmap_b;  // the same tensor, boxes of the compact pass (tile proper only)
+    CUtensorMap tmap_c;  // the same tensor, 64-sample boxes (the streaming form's compaction steps)
     const int16_t *samples;
     int32_t n_calo, n_xtal, n_fills;
     int64_t n_samples;  // row pitch
@@ -120,7 +121,7 @@ struct KArgs {
     // single-launch form: tiles the count role may run ahead of the compact
     // role, and the two progress counters (tiles scanned, tiles compacted)
     int64_t lag_tiles;
-    int32_t pf_dist;  // count pass: L2 prefetch of the CTA's tile pf_dist tiles after the one loaded (0 = none)
+    int32_t str_meta, str_stages;  // streaming form: tile records and row stages per CTA
     unsigned long long *fctr;
     // outputs
     daq_island *hdr;
@@ -218,28 +219,13 @@ __device__ __forceinline__ void issue_tile_load(const KArgs &a, const TileInfo &
 {
     const int c0 = (int)(T.t0 - a.hl);
     const int c1 = (int)(((long long)T.f * a.n_calo + T.c) * a.n_xtal);
-    if (a.mode == kModeFused) {  // the compact role re-reads these lines soon: keep them in L2
+    if (a.mode == kModeFused || a.mode == kModeStream) {  // re-read soon by the compaction: keep them in L2
         const uint64_t pol = l2_policy_evict_last();
         for (int k = 0; k < a.nbox; ++k)
             tma_load_2d_hint(slot + (size_t)k * a.box_stride, &a.tmap, c0 + k * a.boxw, c1, bar, pol);
         return;
     }
     for (int k = 0; k < a.nbox; ++k) tma_load_2d(slot + (size_t)k * a.box_stride, &a.tmap, c0 + k * a.boxw, c1, bar);
-}
-
-// L2 prefetch of the boxes of one tile that lie wholly inside the tensor (one
-// thread).  A hint only: the tile's own load later reads these lines from L2.
-__device__ __forceinline__ void issue_tile_prefetch(const KArgs &a, const TileInfo &T)
-{
-    const int c0 = (int)(T.t0 - a.hl);
-    const int c1 = (int)(((long long)T.f * a.n_calo + T.c) * a.n_xtal);
-    const uint64_t pol = l2_policy_evict_last();
-    for (int k = 0; k < a.nbox; ++k) {
-        const long long col = (long long)c0 + (long long)k * a.boxw;
-        if (col < 0 || col + a.boxw > a.n_samples) continue;
-        if (a.mode == kModeFused || a.mode == kModeStream) tma_prefetch_2d_hint(&a.tmap, (int)col, c1, pol);
-        else tma_prefetch_2d(&a.tmap, (int)col, c1);
-    }
 }
 
 __device__ __forceinline__ uint32_t tile_load_bytes(const KArgs &a)
@@ -550,13 +536,18 @@ __device__ __forceinline__ Agg tile_bits(const KArgs &a, const TileInfo &T, cons
 }
 
 // --------------------------------------------------------------------------- cross-tile scan
-__device__ __forceinline__ void publish(TileStatus *st, long long tile, bool inclusive, const Agg &v)
+__device__ __forceinline__ void publish(TileStatus *st, long long tile, bool inclusive, const Agg &v,
+                                        bool relaxed = false)
 {
     const unsigned long long kind = inclusive ? (v.poison ? kKindPoison : kKindInc) : kKindAgg;
     const unsigned long long lo = ((unsigned long long)v.m << 2) | kind;
     const unsigned long long hi = ((unsigned long long)v.s << 33) | ((unsigned long long)v.tr << 3) |
                                   ((unsigned long long)(v.full != 0) << 2) | kind;
-    st_release_b128(&st[tile], lo, hi);
+    // the word is the whole message (readers use nothing else on its account),
+    // so a relaxed store suffices; release also waits for the thread's earlier
+    // stores and atomics
+    if (relaxed) st_relaxed_b128(&st[tile], lo, hi);
+    else st_release_b128(&st[tile], lo, hi);
 }
 
 // kind of a status read (0 when not yet published or the halves disagree)

@@ -187,11 +187,6 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(full + s, tile_load_bytes(a));
             issue_tile_load(a, T, slot0 + (size_t)s * a.slot_bytes, full + s);
-            if (a.pf_dist > 0) {
-                TileInfo P;
-                if (decode_tile<TW>(a, tile + (long long)a.pf_dist * G, P, plan.fts, plan.lens))
-                    issue_tile_prefetch(a, P);
-            }
         }
         trace_stamp(a, tile, 1);
     };
