@@ -287,7 +287,7 @@ def bench_gb300(args, ws, rank, local):
                        "max": round(max(step_ms), 4)},
         "kernels_ms": {"daq_prepare_kernel": round(statistics.fmean(prep_ms), 4),
                        "daq_count_kernel": round(count_mean, 4),
-                       "daq_scan_kernels": round(statistics.fmean(scan_ms), 4),
+                       "daq_scan_kernel": round(statistics.fmean(scan_ms), 4),
                        "daq_compact_kernel": round(compact_mean, 4)},
         "count_kernel_gbs": round(alg_count / (count_mean * 1e-3) / 1e9, 1),
         "islands_per_fill": n_isl, "pool_rows_per_fill": n_rows,
@@ -560,7 +560,7 @@ def time_calls(torch, dev, daq, x, F, C, X, N, params, K: int, out=None, warm: i
     ms = [r[0].elapsed_time(r[4]) for r in evs]
     total = evs[0][0].elapsed_time(evs[-1][4])
     kern = {name: round(statistics.fmean(r[i].elapsed_time(r[i + 1]) for r in evs), 4)
-            for i, name in enumerate(["daq_prepare_kernel", "daq_count_kernel", "daq_scan_kernels",
+            for i, name in enumerate(["daq_prepare_kernel", "daq_count_kernel", "daq_scan_kernel",
                                       "daq_compact_kernel"])}
     counts = out.counts.cpu().numpy()
     del ws, q

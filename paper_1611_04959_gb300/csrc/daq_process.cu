@@ -65,7 +65,7 @@ static int stage_row_bytes(int X)
 
 // Workspace layout (byte offsets from the workspace base).
 struct WsLayout {
-    size_t ticket, fts, lens, ptot, status, marks, recs, excl, blockagg, total;
+    size_t ticket, fts, lens, ptot, status, marks, recs, excl, scan_status, total;
 };
 
 static WsLayout ws_layout(int64_t n_fills, int64_t n_calo, int64_t max_tiles)
@@ -73,7 +73,7 @@ static WsLayout ws_layout(int64_t n_fills, int64_t n_calo, int64_t max_tiles)
     auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
     WsLayout w;
     w.ticket = 0;
-    w.fts = up(512);  // [0, 16) ticket; 128 and 256: counters of the single-launch form
+    w.fts = up(512);  // [0, 16) ticket; 128 and 256: counters of the single-launch form; 384: scan ticket
     w.lens = up(w.fts + sizeof(long long) * (size_t)(n_fills + 1));
     w.ptot = up(w.lens + sizeof(int32_t) * (size_t)(n_fills > 0 ? n_fills : 1));
     w.status = up(w.ptot + sizeof(int32_t) * (size_t)(n_fills * n_calo > 0 ? n_fills * n_calo : 1));
@@ -81,8 +81,8 @@ static WsLayout ws_layout(int64_t n_fills, int64_t n_calo, int64_t max_tiles)
     w.marks = up(w.status + sizeof(TileStatus) * nt);
     w.recs = up(w.marks + sizeof(uint32_t) * (size_t)(kMaxTileWords) * nt);
     w.excl = up(w.recs + sizeof(TileRec) * nt);
-    w.blockagg = up(w.excl + sizeof(TileExcl) * nt);
-    w.total = up(w.blockagg + sizeof(Agg) * ((nt + kScanChunk - 1) / kScanChunk));
+    w.scan_status = up(w.excl + sizeof(TileExcl) * nt);
+    w.total = up(w.scan_status + sizeof(TileStatus) * ((nt + kScanChunk - 1) / kScanChunk));
     return w;
 }
 
@@ -114,6 +114,12 @@ __global__ void __launch_bounds__(kThreads) daq_prepare_kernel(KArgs a, int tw)
         const long long n16 = a.max_tiles * (long long)(sizeof(TileStatus) / 16);
         for (long long i = (long long)blockIdx.x * kThreads + tid; i < n16; i += (long long)gridDim.x * kThreads)
             st[i] = make_uint4(0u, 0u, 0u, 0u);
+    } else {  // the chained scan's block states and ticket
+        uint4 *st = reinterpret_cast<uint4 *>(a.scan_status);
+        const long long n16 = (a.max_tiles + kScanChunk - 1) / kScanChunk;
+        for (long long i = (long long)blockIdx.x * kThreads + tid; i < n16; i += (long long)gridDim.x * kThreads)
+            st[i] = make_uint4(0u, 0u, 0u, 0u);
+        if (blockIdx.x == 0 && tid == 0) *a.scan_ticket = 0u;
     }
 
     if (blockIdx.x == 0) {
@@ -166,15 +172,47 @@ __global__ void __launch_bounds__(kThreads) daq_prepare_kernel(KArgs a, int tw)
         len = len < 0 ? 0 : (len > a.n_samples ? a.n_samples : len);
         const long long n = len < a.ped_samples ? len : a.ped_samples;
         long long ptot_part = 0;
-        for (int x = warp; x < a.n_xtal; x += kWarps) {
-            const int16_t *row = a.samples + (cf * a.n_xtal + x) * a.n_samples;
-            long long sum = 0;
-            for (long long t = lane; t < n; t += 32) sum += row[t];
+        auto finish = [&](int x, long long sum) {  // warp sum of crystal x's window -> its pedestal
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(kFull, sum, d);
             const long long p = n > 0 ? floor_div_ll(sum + n / 2, n) : 0;
             if (lane == 0 && a.ped_out && !(a.flags & DAQ_SKIP_ISLANDS)) a.ped_out[cf * a.n_xtal + x] = (int32_t)p;
             ptot_part += p;
+        };
+        if (n <= 256 && (a.n_samples & 7) == 0 && (reinterpret_cast<uintptr_t>(a.samples) & 15) == 0) {
+            // lane L sums samples [8L, 8L + 8) of the window with one 16-byte load per
+            // crystal; the loads of kPedX crystals are in flight at once
+            constexpr int kPedX = 8;
+            for (int x0 = warp; x0 < a.n_xtal; x0 += kWarps * kPedX) {
+                int4 v[kPedX];
+#pragma unroll
+                for (int k = 0; k < kPedX; ++k) {
+                    const int x = x0 + k * kWarps;
+                    v[k] = make_int4(0, 0, 0, 0);
+                    if (x < a.n_xtal && 8 * lane < n)
+                        v[k] = __ldg(reinterpret_cast<const int4 *>(a.samples + (cf * a.n_xtal + x) * a.n_samples) + lane);
+                }
+#pragma unroll
+                for (int k = 0; k < kPedX; ++k) {
+                    const int x = x0 + k * kWarps;
+                    if (x >= a.n_xtal) break;
+                    const uint32_t w[4] = {(uint32_t)v[k].x, (uint32_t)v[k].y, (uint32_t)v[k].z, (uint32_t)v[k].w};
+                    long long sum = 0;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int16_t val = (int16_t)((w[j >> 1] >> (16 * (j & 1))) & 0xffffu);
+                        if (8 * lane + j < n) sum += val;
+                    }
+                    finish(x, sum);
+                }
+            }
+        } else {
+            for (int x = warp; x < a.n_xtal; x += kWarps) {
+                const int16_t *row = a.samples + (cf * a.n_xtal + x) * a.n_samples;
+                long long sum = 0;
+                for (long long t = lane; t < n; t += 32) sum += row[t];
+                finish(x, sum);
+            }
         }
         if (lane == 0) s_ped[warp] = ptot_part;
         __syncthreads();
@@ -887,8 +925,7 @@ static cudaError_t launch_twopass(const KArgs &a, const Plan &pl, int grid, int 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
     const int scan_blocks = (int)((tiles + kScanChunk - 1) / kScanChunk);
-    daq_scan_reduce_kernel<<<scan_blocks, kScanThreads, 0, s>>>(a);
-    daq_scan_apply_kernel<<<scan_blocks, kScanThreads, 0, s>>>(a);
+    daq_scan_kernel<<<scan_blocks, kScanThreads, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
     if (!skip_isl) {
@@ -1105,7 +1142,8 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
     a.marks = reinterpret_cast<uint32_t *>(ws + wl.marks);
     a.recs = ws + wl.recs;
     a.excl = ws + wl.excl;
-    a.blockagg = reinterpret_cast<Agg *>(ws + wl.blockagg);
+    a.scan_status = reinterpret_cast<TileStatus *>(ws + wl.scan_status);
+    a.scan_ticket = reinterpret_cast<unsigned int *>(ws + 384);
     a.trace = reinterpret_cast<unsigned long long *>(p.trace);
 
     cudaStream_t s = static_cast<cudaStream_t>(p.stream);

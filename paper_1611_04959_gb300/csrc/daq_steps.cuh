@@ -140,7 +140,8 @@ struct KArgs {
     uint32_t *marks;             // two-pass: [max_tiles][TW/32] marks words of each tile
     void *recs;                  // two-pass: [max_tiles] tile aggregates
     void *excl;                  // two-pass: [max_tiles] exclusive prefixes
-    Agg *blockagg;               // two-pass: [scan blocks] aggregates of each scan block
+    TileStatus *scan_status;     // two-pass: [scan blocks] published aggregate / inclusive prefix of each block
+    unsigned int *scan_ticket;   // two-pass: scan block order
     unsigned long long *trace;   // NULL or [max_tiles][16] stage stamps
 };
 
@@ -574,10 +575,9 @@ __device__ __forceinline__ unsigned read_status(const TileStatus *st, long long 
 // latest entries up to and including the first one that is not fully marked.
 // Bounded: gives up after kWaitLimitNs or once another CTA has flagged a
 // timeout, returning a poisoned prefix.
-__device__ Agg look_back(const KArgs &a, long long tile, int lane, unsigned *stats = nullptr)
+__device__ Agg look_back_in(const KArgs &a, const TileStatus *st, long long tile, int lane, unsigned *stats = nullptr)
 {
     constexpr int PER = 4, BIG = 1 << 20;
-    const TileStatus *st = a.status;
     long long pos = tile - 1;
     Agg acc = agg_identity();
     uint64_t t_start = 0;
@@ -665,6 +665,11 @@ __device__ Agg look_back(const KArgs &a, long long tile, int lane, unsigned *sta
         pos -= 32 * PER;
         waiting = false;
     }
+}
+
+__device__ __forceinline__ Agg look_back(const KArgs &a, long long tile, int lane, unsigned *stats = nullptr)
+{
+    return look_back_in(a, a.status, tile, lane, stats);
 }
 
 // --------------------------------------------------------------------------- pool rows to global

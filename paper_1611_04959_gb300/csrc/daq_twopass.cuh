@@ -331,39 +331,23 @@ __device__ __forceinline__ Agg block_scan_incl(Agg v, Agg *warp_tot, Agg *block_
     return v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) daq_scan_reduce_kernel(const __grid_constant__ KArgs a)
-{
-    __shared__ Agg warp_tot[kScanThreads / 32];
-    const long long total = a.fill_tile_start[a.n_fills];
-    const long long base = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanPer;
-    const TileRec *recs = reinterpret_cast<const TileRec *>(a.recs);
-    Agg v = agg_identity();
-    for (int i = 0; i < kScanPer; ++i)
-        if (base + i < total) v = combine(v, rec_agg(recs[base + i]));
-    Agg tot;
-    block_scan_incl(v, warp_tot, &tot);
-    if (threadIdx.x == 0) a.blockagg[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(kScanThreads) daq_scan_apply_kernel(const __grid_constant__ KArgs a)
+// Single-launch chained scan: blocks take chunks of kScanChunk tiles in ticket
+// order (so every chunk's predecessors are running or done); each reduces its chunk,
+// publishes the aggregate, looks back over earlier chunks' published states
+// for its exclusive prefix (one warp), publishes its inclusive prefix and
+// writes every tile's exclusive prefix.
+__global__ void __launch_bounds__(kScanThreads) daq_scan_kernel(const __grid_constant__ KArgs a)
 {
     __shared__ Agg warp_tot[kScanThreads / 32];
     __shared__ Agg s_incl[kScanThreads];
     __shared__ Agg s_prefix;
+    __shared__ long long s_chunk;
+    if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(a.scan_ticket, 1u);
+    __syncthreads();
+    const long long chunk = s_chunk;
     const long long total = a.fill_tile_start[a.n_fills];
-    const long long chunk0 = (long long)blockIdx.x * kScanChunk;
-    if (chunk0 >= total) return;
-    {   // prefix of the earlier blocks: each thread combines a contiguous run of
-        // block aggregates, then an ordered block scan joins the runs
-        const unsigned nb = blockIdx.x, per = (nb + kScanThreads - 1) / kScanThreads;
-        const unsigned lo = threadIdx.x * per, hi = min(nb, lo + per);
-        Agg p = agg_identity();
-        for (unsigned b = lo; b < hi; ++b) p = combine(p, a.blockagg[b]);
-        Agg all;
-        block_scan_incl(p, warp_tot, &all);
-        if (threadIdx.x == 0) s_prefix = all;
-        __syncthreads();
-    }
+    const long long chunk0 = chunk * kScanChunk;
+    if (chunk0 >= total) return;  // grids are sized for the largest tile count
     const long long base = chunk0 + (long long)threadIdx.x * kScanPer;
     const TileRec *recs = reinterpret_cast<const TileRec *>(a.recs);
     TileRec r[kScanPer];
@@ -375,8 +359,21 @@ __global__ void __launch_bounds__(kScanThreads) daq_scan_apply_kernel(const __gr
     }
     Agg blk_tot;
     s_incl[threadIdx.x] = block_scan_incl(v, warp_tot, &blk_tot);
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        Agg ex = agg_identity();
+        if (chunk > 0) {
+            if (lane == 0) publish(a.scan_status, chunk, false, blk_tot, true);
+            ex = look_back_in(a, a.scan_status, chunk, lane);
+        }
+        if (lane == 0) {
+            publish(a.scan_status, chunk, true, combine(ex, blk_tot), true);
+            s_prefix = ex;
+        }
+    }
     __syncthreads();
-    Agg ex = threadIdx.x == 0 ? s_prefix : combine(s_prefix, s_incl[threadIdx.x - 1]);
+    const Agg prefix = s_prefix;
+    Agg ex = threadIdx.x == 0 ? prefix : combine(prefix, s_incl[threadIdx.x - 1]);
     TileExcl *out = reinterpret_cast<TileExcl *>(a.excl);
 #pragma unroll
     for (int i = 0; i < kScanPer; ++i) {
