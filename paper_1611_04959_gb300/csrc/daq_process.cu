@@ -697,6 +697,8 @@ static DeviceInfo device_info(int dev)
 // Shared memory one CTA may use, for planning before any device is queried
 // (GB300: 227 KB).
 constexpr int kSmemBudget = 227 * 1024;
+constexpr int kSmemPerSM = 228 * 1024;         // shared memory of one SM
+constexpr int kSmemPerBlockReserved = 1024;    // reserved by the system for each resident CTA
 // Single-launch form: default and least distance (tiles) the count role may
 // run ahead of the compact role.  The least is the scanner's round (one block
 // of tiles), below which the roles could wait on each other forever.
@@ -708,6 +710,7 @@ struct Plan {
     int boxw_b, nbox_b, box_stride_b, slot_bytes_b, rs_b;  // compact pass (two-pass mode)
     size_t smem, smem_b;                                   // tile (or count) kernel, compact kernel
     int str_meta, str_stages;                              // streaming form: tile records, row stages per CTA
+    int count_ns;                                          // two-pass form: tile slots of the count kernel (2 or 3)
     int64_t max_tiles;
 };
 
@@ -774,6 +777,15 @@ static void plan_geometry(Plan *pl, int tw, int pre, int post, int X)
         pl->smem = plain_smem_bytes(tw, X, pl->slot_bytes, pl->rs, pl->need_sarr);
     } else {
         pl->smem = count_smem_bytes(tw, pl->slot_bytes, pl->need_sarr);
+        pl->count_ns = 2;
+        if (pl->mode == kModeTwoPass && 2 * (pl->smem + kSmemPerBlockReserved) > (size_t)kSmemPerSM) {
+            // two CTAs with two slots each do not fit: one CTA with three slots
+            const size_t s3 = CountSmemT<3>::total(pl->slot_bytes, tw, pl->need_sarr);
+            if (s3 <= (size_t)kSmemBudget) {
+                pl->smem = s3;
+                pl->count_ns = 3;
+            }
+        }
         pl->smem_b = compact_smem_bytes(tw, X, pl->slot_bytes_b);
         if (pl->mode == kModeFused) {  // one kernel holds either role
             pl->smem = std::max(pl->smem, pl->smem_b);
@@ -902,8 +914,11 @@ template <int TW>
 static cudaError_t launch_twopass(const KArgs &a, const Plan &pl, int grid, int sms, bool skip_isl,
                                   cudaEvent_t const *ev, cudaStream_t s)
 {
-    static size_t conf_a[64] = {0}, conf_b[64] = {0};
-    cudaError_t e = ensure_smem(daq_count_kernel<TW>, pl.smem, conf_a);
+    static size_t conf_a[64] = {0}, conf_a3[64] = {0}, conf_b[64] = {0};
+    const bool ns3 = pl.count_ns == 3;
+    const int count_thr = ns3 ? count_threads<3>() : count_threads<2>();
+    cudaError_t e = ns3 ? ensure_smem(daq_count_kernel<TW, 3>, pl.smem, conf_a3)
+                        : ensure_smem(daq_count_kernel<TW, 2>, pl.smem, conf_a);
     if (e != cudaSuccess) return e;
     e = ensure_smem(daq_compact_kernel<TW>, pl.smem_b, conf_b);
     if (e != cudaSuccess) return e;
@@ -911,7 +926,8 @@ static cudaError_t launch_twopass(const KArgs &a, const Plan &pl, int grid, int 
     int grid_a = grid, grid_b = grid;
     if (grid <= 0) {
         int per_a = 0, per_b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_a, daq_count_kernel<TW>, kCountThreads, pl.smem);
+        e = ns3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_a, daq_count_kernel<TW, 3>, count_thr, pl.smem)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_a, daq_count_kernel<TW, 2>, count_thr, pl.smem);
         if (e != cudaSuccess) return e;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_b, daq_compact_kernel<TW>, 256, pl.smem_b);
         if (e != cudaSuccess) return e;
@@ -921,7 +937,8 @@ static cudaError_t launch_twopass(const KArgs &a, const Plan &pl, int grid, int 
     }
     grid_a = (int)std::min<int64_t>(grid_a, tiles);
     grid_b = (int)std::min<int64_t>(grid_b, tiles);
-    daq_count_kernel<TW><<<grid_a, kCountThreads, pl.smem, s>>>(a);
+    if (ns3) daq_count_kernel<TW, 3><<<grid_a, count_thr, pl.smem, s>>>(a);
+    else daq_count_kernel<TW, 2><<<grid_a, count_thr, pl.smem, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
     const int scan_blocks = (int)((tiles + kScanChunk - 1) / kScanChunk);

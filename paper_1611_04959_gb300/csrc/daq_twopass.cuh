@@ -57,7 +57,7 @@ __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.
 
 // ============================================================================ count pass
 constexpr int kCountSumWarps = 8;
-constexpr int kCountThreads = 32 * (kCountSumWarps + 2);  // + two marks/Q warps, one per buffer
+constexpr int kCountThreads = 32 * (kCountSumWarps + 2);  // + one marks/Q warp per tile slot (two slots)
 constexpr int kPlanSmem = 64;                              // fills whose plan is cached in shared memory
 
 // Per-fill plan (first tile, length) in shared memory when the batch has at
@@ -82,19 +82,23 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
     return !__any_sync(kFull, !ok);
 }
 
-// Shared-memory layout of the count kernel, in the order of the buffers.
-struct CountSmem {
+// Shared-memory layout of the count kernel with NS tile slots, in the order of
+// the buffers.
+template <int NS> struct CountSmemT {
     static size_t __host__ __device__ align16(size_t x) { return (x + 15) & ~size_t(15); }
-    static size_t __host__ __device__ abyte(int slot_bytes) { return 2 * (size_t)slot_bytes; }            // [2][128]
-    static size_t __host__ __device__ blocksum(int slot_bytes) { return abyte(slot_bytes) + 256; }          // [2][TW/8]
-    static size_t __host__ __device__ sarr(int slot_bytes, int tw) { return blocksum(slot_bytes) + (size_t)tw; }  // [2][TW]
+    static size_t __host__ __device__ abyte(int slot_bytes) { return NS * (size_t)slot_bytes; }  // [NS][128]
+    static size_t __host__ __device__ blocksum(int slot_bytes) { return abyte(slot_bytes) + 128 * NS; }  // [NS][TW/8]
+    static size_t __host__ __device__ sarr(int slot_bytes, int tw)  // [NS][TW]
+    {
+        return blocksum(slot_bytes) + (size_t)NS * (size_t)(tw / 8) * 4;
+    }
     static size_t __host__ __device__ tinfo(int slot_bytes, int tw, int need_sarr)
     {
-        return align16(sarr(slot_bytes, tw) + (need_sarr ? 8 * (size_t)tw : 0));  // [4]
+        return align16(sarr(slot_bytes, tw) + (need_sarr ? (size_t)NS * 4 * (size_t)tw : 0));  // [2 NS]
     }
     static size_t __host__ __device__ fts(int slot_bytes, int tw, int need_sarr)
     {
-        return tinfo(slot_bytes, tw, need_sarr) + 4 * sizeof(TileInfo);  // [kPlanSmem + 1]
+        return tinfo(slot_bytes, tw, need_sarr) + 2 * NS * sizeof(TileInfo);  // [kPlanSmem + 1]
     }
     static size_t __host__ __device__ lens(int slot_bytes, int tw, int need_sarr)
     {
@@ -102,13 +106,18 @@ struct CountSmem {
     }
     static size_t __host__ __device__ bars(int slot_bytes, int tw, int need_sarr)
     {
-        return align16(lens(slot_bytes, tw, need_sarr) + 4 * kPlanSmem);  // full[2], sums[2], marks[2]
+        return align16(lens(slot_bytes, tw, need_sarr) + 4 * kPlanSmem);  // full[NS], sums[NS], marks[NS]
     }
     static size_t __host__ __device__ total(int slot_bytes, int tw, int need_sarr)
     {
-        return (bars(slot_bytes, tw, need_sarr) + 6 * 8 + 127) & ~size_t(127);
+        return (bars(slot_bytes, tw, need_sarr) + 3 * NS * 8 + 127) & ~size_t(127);
     }
 };
+using CountSmem = CountSmemT<2>;
+// Sum warps of the count kernel: 8 with two slots (two CTAs per SM), 16 with
+// three (one CTA per SM keeps the SM's sum throughput).
+template <int NS> __host__ __device__ constexpr int count_sum_warps() { return NS == 2 ? kCountSumWarps : 2 * kCountSumWarps; }
+template <int NS> __host__ __device__ constexpr int count_threads() { return 32 * (count_sum_warps<NS>() + NS); }
 
 // Progress counters of the single-launch form (workspace words).
 __device__ __forceinline__ unsigned long long *scanned_ctr(const KArgs &a) { return a.fctr; }
@@ -134,37 +143,40 @@ __device__ __forceinline__ bool wait_counter_ge(const KArgs &a, const unsigned l
 }
 
 // Eight sum warps turn a tile into threshold bits and block sums; marks warp
-// s (one per buffer s = j & 1) turns the bits of the CTA's tiles j = s, s + 2,
-// ... into marks words and the tile aggregate and adds the tile's Q bins, while
-// the sum warps go on with the next tile.  Two tile slots are loaded ahead by
-// TMA.  Handoffs (per buffer): full (TMA landed), sums (8 sum warps done: the
+// s (one per buffer s = j mod NS) turns the bits of the CTA's tiles j = s,
+// s + NS, ... into marks words and the tile aggregate and adds the tile's Q
+// bins, while the sum warps go on with the next tile.  NS tile slots are
+// loaded ahead by TMA.  Handoffs (per buffer): full (TMA landed), sums (8 sum warps done: the
 // slot may be refilled and the bits read), marks (bits and block sums read:
 // the buffer may be rewritten).  The CTA takes tiles first, first + G, ...
 // kFused: a tile is loaded only while it is at most lag_tiles ahead of the
 // tiles compacted, and its aggregate is published with a release store and a
 // valid bit for the scanner.
-template <int TW, bool kFused>
+template <int TW, bool kFused, int NS = 2>
 __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, long long first, long long G)
 {
     constexpr int NWT = TW / 32, NBT = TW / 8;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned char *slot0 = smem;
-    uint8_t *abyte0 = smem + CountSmem::abyte(a.slot_bytes);
-    int32_t *blocksum0 = reinterpret_cast<int32_t *>(smem + CountSmem::blocksum(a.slot_bytes));
-    int32_t *sarr0 = reinterpret_cast<int32_t *>(smem + CountSmem::sarr(a.slot_bytes, TW));
-    TileInfo *tinfo = reinterpret_cast<TileInfo *>(smem + CountSmem::tinfo(a.slot_bytes, TW, a.need_sarr));
-    TileInfo *tinfo_m = tinfo + 2;  // copies handed to the marks warps
-    long long *fts_s = reinterpret_cast<long long *>(smem + CountSmem::fts(a.slot_bytes, TW, a.need_sarr));
-    int32_t *lens_s = reinterpret_cast<int32_t *>(smem + CountSmem::lens(a.slot_bytes, TW, a.need_sarr));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + CountSmem::bars(a.slot_bytes, TW, a.need_sarr));
-    uint64_t *full = bars, *sums = bars + 2, *mdone = bars + 4;
+    using SM = CountSmemT<NS>;
+    constexpr int kThr = count_threads<NS>();
+    constexpr int NSW = count_sum_warps<NS>();
+    uint8_t *abyte0 = smem + SM::abyte(a.slot_bytes);
+    int32_t *blocksum0 = reinterpret_cast<int32_t *>(smem + SM::blocksum(a.slot_bytes));
+    int32_t *sarr0 = reinterpret_cast<int32_t *>(smem + SM::sarr(a.slot_bytes, TW));
+    TileInfo *tinfo = reinterpret_cast<TileInfo *>(smem + SM::tinfo(a.slot_bytes, TW, a.need_sarr));
+    TileInfo *tinfo_m = tinfo + NS;  // copies handed to the marks warps
+    long long *fts_s = reinterpret_cast<long long *>(smem + SM::fts(a.slot_bytes, TW, a.need_sarr));
+    int32_t *lens_s = reinterpret_cast<int32_t *>(smem + SM::lens(a.slot_bytes, TW, a.need_sarr));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM::bars(a.slot_bytes, TW, a.need_sarr));
+    uint64_t *full = bars, *sums = bars + NS, *mdone = bars + 2 * NS;
 
-    for (int i = tid; i < 64; i += kCountThreads) reinterpret_cast<uint32_t *>(abyte0)[i] = 0u;
-    const PlanView plan = cache_plan(a, fts_s, lens_s, tid, kCountThreads);
+    for (int i = tid; i < 32 * NS; i += kThr) reinterpret_cast<uint32_t *>(abyte0)[i] = 0u;
+    const PlanView plan = cache_plan(a, fts_s, lens_s, tid, kThr);
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(full + s, 1);
-            mbar_init(sums + s, kCountSumWarps);
+            mbar_init(sums + s, NSW);
             mbar_init(mdone + s, 1);
         }
         fence_mbar_init();
@@ -172,7 +184,7 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
     __syncthreads();
     const long long total = plan.fts[a.n_fills];
     const int n_steps = (a.ew + 63) / 64;
-    constexpr int kSumThreads = 32 * kCountSumWarps;
+    constexpr int kSumThreads = 32 * NSW;
 
     auto start_load = [&](long long tile, int s) {  // thread 0
         if (kFused &&
@@ -191,16 +203,15 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
         trace_stamp(a, tile, 1);
     };
 
-    if (warp < kCountSumWarps) {
-        if (tid == 0) {
-            if (first < total) start_load(first, 0);
-            if (first + G < total) start_load(first + G, 1);
-        }
+    if (warp < NSW) {
+        if (tid == 0)
+            for (int k = 0; k < NS; ++k)
+                if (first + k * G < total) start_load(first + k * G, k);
         for (long long j = 0;; ++j) {
             const long long tile = first + j * G;
             if (tile >= total) break;
-            const int s = (int)(j & 1);
-            const uint32_t par = (uint32_t)((j >> 1) & 1);
+            const int s = (int)(j % NS);
+            const uint32_t par = (uint32_t)((j / NS) & 1);
             unsigned char *slot = slot0 + (size_t)s * a.slot_bytes;
             if (a.use_tma) {
                 if (!warp_wait(full + s, par)) {
@@ -213,7 +224,7 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
                 plain_tile_load(a, tinfo[s], slot, tid, kSumThreads);
                 asm volatile("bar.sync 1, %0;" ::"r"(kSumThreads) : "memory");
             }
-            if (j >= 2 && !warp_wait(mdone + s, par ^ 1u)) {
+            if (j >= NS && !warp_wait(mdone + s, par ^ 1u)) {
                 if (lane == 0) set_status_bit(a, DAQ_DEV_TIMEOUT);
                 break;
             }
@@ -223,32 +234,32 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
                 tinfo_m[s] = T;
             }
             const uint32_t slot_s = smem_addr(slot);
-            for (int it = warp; it < n_steps; it += kCountSumWarps)
+            for (int it = warp; it < n_steps; it += NSW)
                 sum_pass_step(a, T, slot_s, it, NBT, abyte0 + 128 * s, blocksum0 + NBT * s,
                               sarr0 + (a.need_sarr ? TW * s : 0), nullptr, lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(sums + s);
             if (tid == 0) {
                 trace_stamp(a, T.tile, 3);
-                // slot s takes tile j + 2 once every sum warp is done with tile j
-                if (tile + 2 * G < total) {
+                // slot s takes tile j + NS once every sum warp is done with tile j
+                if (tile + NS * G < total) {
                     if (mbar_wait_bounded(sums + s, par, kWaitLimitNs)) {
-                        if (a.use_tma) start_load(tile + 2 * G, s);
-                        else decode_tile<TW>(a, tile + 2 * G, tinfo[s], plan.fts, plan.lens);
+                        if (a.use_tma) start_load(tile + NS * G, s);
+                        else decode_tile<TW>(a, tile + NS * G, tinfo[s], plan.fts, plan.lens);
                     } else {
                         set_status_bit(a, DAQ_DEV_TIMEOUT);  // the other warps time out on tile j + 2
                     }
                 }
             }
         }
-    } else if (warp < kCountSumWarps + 2) {
+    } else if (warp < NSW + NS) {
         // ------------------------------------------------------------ marks, aggregate, Q bins of buffer s
-        const int s = warp - kCountSumWarps;
+        const int s = warp - NSW;
         const bool skip_q = (a.flags & DAQ_SKIP_Q) != 0;
-        for (long long j = s;; j += 2) {
+        for (long long j = s;; j += NS) {
             const long long tile = first + j * G;
             if (tile >= total) break;
-            if (!warp_wait(sums + s, (uint32_t)((j >> 1) & 1))) {
+            if (!warp_wait(sums + s, (uint32_t)((j / NS) & 1))) {
                 if (lane == 0) set_status_bit(a, DAQ_DEV_TIMEOUT);
                 break;
             }
@@ -286,11 +297,13 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
     }
 }
 
-template <int TW>
-__global__ void __launch_bounds__(kCountThreads, 2) daq_count_kernel(const __grid_constant__ KArgs a)
+// NS = 2: two CTAs per SM; NS = 3: one CTA per SM with 16 sum warps, for
+// extended tiles too wide for two CTAs' slots to fit.
+template <int TW, int NS>
+__global__ void __launch_bounds__(count_threads<NS>(), NS == 2 ? 2 : 1) daq_count_kernel(const __grid_constant__ KArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    count_role<TW, false>(a, smem, blockIdx.x, gridDim.x);
+    count_role<TW, false, NS>(a, smem, blockIdx.x, gridDim.x);
 }
 
 // ============================================================================ scan of the aggregates

@@ -67,8 +67,13 @@ def main():
     ap.add_argument("--flags", type=int, default=0, help="daq_params.flags (1 = skip Q, 2 = skip islands)")
     ap.add_argument("--lag", type=int, default=0, help="daq_params.lag_tiles (single-launch form, grid -4)")
     ap.add_argument("--out", default=None, help="save the raw trace (.npy)")
+    ap.add_argument("--stress", type=int, default=0,
+                    help="trace this many fills of the stress workload (10x rate, T=15, post=64, D=8 and 32) instead")
     args = ap.parse_args()
-    w = W.scaled(W.PLAIN_FULL_FILL, n_calo=args.calos)
+    if args.stress:
+        w = W.scaled(W.STRESS, n_fills=args.stress, n_calo=args.calos)
+    else:
+        w = W.scaled(W.PLAIN_FULL_FILL, n_calo=args.calos)
     s = torch.from_numpy(synth.generate(w.config())).cuda()
     F, C, X, N = s.shape
     p = daq.make_params(**w.params(), tile=args.tile, grid=args.grid, lag_tiles=args.lag)
