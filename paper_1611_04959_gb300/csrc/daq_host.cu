@@ -22,7 +22,7 @@
 namespace {
 
 constexpr int kMaxChunks = 64;
-constexpr int kTargetChunks = 24;  // finer chunks shorten the unoverlapped first copy-in and last copy-out
+constexpr int kTargetChunks = 8;
 constexpr int kMaxDevices = 64;
 
 // Streams, events and count buffers of the pipeline, created on a device's
