@@ -44,11 +44,14 @@ def measured_peaks() -> tuple:
         return 6800.0, "fallback"
 
 
+# Sources compiled into the two-pass kernels (prepare, count, scan, compact).
+KERNEL_SOURCES = ("daq_device.cuh", "daq_steps.cuh", "daq_twopass.cuh", "daq_process.cu")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_1611_04959_gb300", "csrc", "*.cu*")))
-    for fn in files:
-        h.update(open(fn, "rb").read())
+    for name in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1611_04959_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
 

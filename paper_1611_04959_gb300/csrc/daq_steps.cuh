@@ -298,7 +298,7 @@ __device__ __forceinline__ void sum_pass_step(const KArgs &a, const TileInfo &T,
     uint32_t *row1 = row0 + (a.srow >> 2);
     int acc0 = 0, acc1 = 0;
     if (have) {
-#pragma unroll 3
+#pragma unroll 9
         for (int x = 0; x < X; x += 2) {
             const uint32_t w0 = lds_u32(base + (uint32_t)(x * a.rs));
             const uint32_t w1 = x + 1 < X ? lds_u32(base + (uint32_t)((x + 1) * a.rs)) : 0u;
