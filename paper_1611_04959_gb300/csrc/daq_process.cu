@@ -714,13 +714,14 @@ struct Plan {
     int64_t max_tiles;
 };
 
-// Box geometry of `width` samples: nbox boxes of boxw <= 248 samples, boxw an
-// odd multiple of 8 (box rows are then an odd multiple of 16 bytes).
+// Box geometry of `width` samples for the compact pass: nbox boxes of boxw <=
+// 248 samples, boxw a multiple of 8.  The compact pass reads along rows, so
+// any row pitch is conflict-free; boxes that split the tile exactly read no
+// column of the next tile.
 static void box_geometry(int width, int X, int *nbox, int *boxw, int *box_stride)
 {
     *nbox = (width + 247) / 248;
-    int bw = (((width + *nbox - 1) / *nbox) + 7) & ~7;
-    if (((bw / 8) & 1) == 0) bw += 8;
+    const int bw = (((width + *nbox - 1) / *nbox) + 7) & ~7;
     *boxw = bw;
     *box_stride = (X * 2 * bw + 127) & ~127;
 }
