@@ -33,6 +33,19 @@ struct __align__(16) TileRec {
     int32_t m, s, tr, flags;  // flags: 1 continues (full), 2 mark before the tile, 4 mark after it
 };
 constexpr int32_t kRecValid = 0x100;  // single-launch form: the record has been published
+constexpr int kRecStepShift = 16;     // flags bits 16..: the tile's 64-sample steps that hold a marked sample
+
+// Bit j set when marks words 2j or 2j + 1 of the tile are non-zero (one warp,
+// lane w holding word w; warp-uniform result).
+template <int TW> __device__ __forceinline__ uint32_t marked_steps64(uint32_t Mt, int lane)
+{
+    constexpr int NWT = TW / 32;
+    const uint32_t nz = __ballot_sync(kFull, lane < NWT && Mt != 0u);
+    uint32_t steps = 0;
+#pragma unroll
+    for (int j = 0; j < (NWT + 1) / 2; ++j) steps |= ((nz >> (2 * j)) & 3u) ? (1u << j) : 0u;
+    return steps;
+}
 
 struct __align__(16) TileExcl {
     long long m;  // pool rows before the tile
@@ -267,6 +280,7 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
             unsigned edges;
             const uint32_t Mt = tile_marks<TW>(a, T, abyte0 + 128 * s, &edges, lane);
             const Agg agg = agg_from_marks<TW>(Mt, edges & 1u, (int)(T.t_end - T.t0), lane);
+            const uint32_t steps = marked_steps64<TW>(Mt, lane);
             if (lane < NWT) a.marks[T.tile * NWT + lane] = Mt;
             if (kFused) {
                 __threadfence();
@@ -277,7 +291,8 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
                 r.m = (int32_t)agg.m;
                 r.s = (int32_t)agg.s;
                 r.tr = (int32_t)agg.tr;
-                r.flags = (agg.full ? 1 : 0) | (int)((edges & 1u) << 1) | (int)((edges >> 1) << 2);
+                r.flags = (agg.full ? 1 : 0) | (int)((edges & 1u) << 1) | (int)((edges >> 1) << 2) |
+                          (int)(steps << kRecStepShift);
                 if (kFused) {
                     // marks words first, then the record with its valid bit (release)
                     __threadfence();
@@ -439,19 +454,20 @@ __device__ __forceinline__ void compact_step(const KArgs &a, uint32_t slot_s, in
     }
 }
 
+// Load the boxes of the tile proper whose bit is set in `boxes` (one thread;
+// the caller armed `bar` for their bytes).
 __device__ __forceinline__ void issue_tile_load_b(const KArgs &a, const TileInfo &T, unsigned char *slot,
-                                                  uint64_t *bar)
+                                                  uint64_t *bar, uint32_t boxes)
 {
     const int c0 = (int)T.t0;
     const int c1 = (int)(((long long)T.f * a.n_calo + T.c) * a.n_xtal);
-    if (a.mode == kModeFused || a.mode == kModeStream) {  // last use of these lines
-        const uint64_t pol = l2_policy_evict_first();
-        for (int k = 0; k < a.nbox_b; ++k)
-            tma_load_2d_hint(slot + (size_t)k * a.box_stride_b, &a.tmap_b, c0 + k * a.boxw_b, c1, bar, pol);
-        return;
+    const bool last_use = a.mode == kModeFused || a.mode == kModeStream;
+    const uint64_t pol = l2_policy_evict_first();
+    for (int k = 0; k < a.nbox_b; ++k) {
+        if (!((boxes >> k) & 1u)) continue;
+        if (last_use) tma_load_2d_hint(slot + (size_t)k * a.box_stride_b, &a.tmap_b, c0 + k * a.boxw_b, c1, bar, pol);
+        else tma_load_2d(slot + (size_t)k * a.box_stride_b, &a.tmap_b, c0 + k * a.boxw_b, c1, bar);
     }
-    for (int k = 0; k < a.nbox_b; ++k)
-        tma_load_2d(slot + (size_t)k * a.box_stride_b, &a.tmap_b, c0 + k * a.boxw_b, c1, bar);
 }
 
 __device__ __forceinline__ void plain_tile_load_b(const KArgs &a, const TileInfo &T, unsigned char *slot, int tid,
@@ -497,6 +513,7 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
     uint64_t *bar = reinterpret_cast<uint64_t *>(s_agg + 1);
     long long *fts_s = reinterpret_cast<long long *>(bar + 1);             // [kPlanSmem + 1]
     int32_t *lens_s = reinterpret_cast<int32_t *>(fts_s + kPlanSmem + 1);  // [kPlanSmem]
+    uint32_t *s_boxes = reinterpret_cast<uint32_t *>(lens_s + kPlanSmem);  // boxes of the CTA's next tile
     const PlanView plan = cache_plan(a, fts_s, lens_s, tid, nthr);
     if (tid == 0) {
         mbar_init(bar, 1);
@@ -506,19 +523,39 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
     const long long total = plan.fts[a.n_fills];
     const TileRec *recs = reinterpret_cast<const TileRec *>(a.recs);
     const TileExcl *exs = reinterpret_cast<const TileExcl *>(a.excl);
-    const uint32_t box_bytes = (uint32_t)a.nbox_b * (uint32_t)X * (uint32_t)a.rs_b;
-
-    auto start_load = [&](long long tile) {  // one thread
+    const uint32_t one_box = (uint32_t)X * (uint32_t)a.rs_b;
+    const uint32_t all_boxes = (1u << a.nbox_b) - 1u;
+    // Boxes of a tile to load: those covering a 64-sample step its count record
+    // marks (box k holds columns [k boxw, (k + 1) boxw)); the single-launch
+    // form's records may not be published yet: all.
+    auto flags_of = [&](long long tile) -> uint32_t {
+        return (kFused || tile >= total) ? ~0u : (uint32_t)recs[tile].flags;
+    };
+    auto boxes_of = [&](uint32_t flags) -> uint32_t {
+        if (flags == ~0u) return all_boxes;
+        const uint32_t steps = flags >> kRecStepShift;
+        uint32_t boxes = 0;
+        for (int k = 0; k < a.nbox_b; ++k) {
+            const int s0 = (k * a.boxw_b) >> 6, s1 = ((k + 1) * a.boxw_b - 1) >> 6;
+            const uint32_t m = (s1 >= 31 ? 0xffffffffu : ((2u << s1) - 1u)) & ~((1u << s0) - 1u);
+            if (steps & m) boxes |= 1u << k;
+        }
+        return boxes;
+    };
+    auto start_load = [&](long long tile, uint32_t boxes) {  // one thread
         decode_tile<TW>(a, tile, *tinfo, plan.fts, plan.lens);
         trace_stamp(a, tile, 5);
         if (a.use_tma) {
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(bar, box_bytes);
-            issue_tile_load_b(a, *tinfo, slot, bar);
+            mbar_arrive_expect_tx(bar, (uint32_t)__popc(boxes) * one_box);
+            issue_tile_load_b(a, *tinfo, slot, bar, boxes);
         }
     };
-    // warp 0's inputs of the next tile, in registers; false if the wait gave up
-    auto load_inputs = [&](long long tile, uint32_t &Mt, TileRec &r, TileExcl &e) -> bool {
+
+    // warp 0's inputs of the next tile, in registers, and (lane 0) the record
+    // flags of the tile after it; false if the wait gave up
+    auto load_inputs = [&](long long tile, uint32_t &Mt, TileRec &r, TileExcl &e, uint32_t &fl2) -> bool {
+        fl2 = lane == 0 ? flags_of(tile + G) : 0u;
         if (kFused) {
             int ok = 1;
             if (lane == 0) ok = wait_counter_ge(a, scanned_ctr(a), (unsigned long long)tile + 1ull) ? 1 : 0;
@@ -540,13 +577,13 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
 
     uint32_t phase_bit = 0;
     bool store_pending = false;
-    uint32_t nMt = 0;
+    uint32_t nMt = 0, nfl2 = 0;
     TileRec nr{0, 0, 0, 0};
     TileExcl ne{0, 0, 0};
     int in_ok = 1;
     if (first < total) {
-        if (tid == 32) start_load(first);
-        if (warp == 0) in_ok = load_inputs(first, nMt, nr, ne) ? 1 : 0;
+        if (tid == 32) start_load(first, boxes_of(flags_of(first)));
+        if (warp == 0) in_ok = load_inputs(first, nMt, nr, ne, nfl2) ? 1 : 0;
     }
     for (long long tile = first; tile < total; tile += G) {
         if (__syncthreads_or(!in_ok)) break;  // tinfo holds this tile; warp 0 has its inputs
@@ -556,6 +593,7 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
             const Agg g = words_from_marks<TW>(nMt, (nr.flags >> 1) & 1, (nr.flags >> 2) & 1,
                                                (int)(T.t_end - T.t0), W, nullptr, lane);
             if (lane == 0) {
+                *s_boxes = boxes_of(nfl2);  // read with this tile's inputs; the next load uses it
                 Agg ex;
                 ex.m = ne.m;
                 ex.s = ne.s;
@@ -592,8 +630,8 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
         if (kFused && tid == 0) atomicAdd(compacted_ctr(a), 1ull);
         const long long next = tile + G;
         if (next < total) {
-            if (tid == 32) start_load(next);
-            if (warp == 0) in_ok = load_inputs(next, nMt, nr, ne) ? 1 : 0;
+            if (tid == 32) start_load(next, *s_boxes);
+            if (warp == 0) in_ok = load_inputs(next, nMt, nr, ne, nfl2) ? 1 : 0;
         }
         if (tid == 0) trace_stamp(a, tile, 7);
         // rows [ex.m, ex.m + agg.m) <- stage bytes [phase, phase + agg.m * 2X)
