@@ -315,56 +315,7 @@ def bench_gb300(args, ws, rank, local):
         "clocks": clocks.summary(),
     }
 
-    # ---- batched form: 16 uneven fills in one tuned, graph-captured launch
-    if not args.no_batched and not args.quick:
-        result["batched"] = bench_batched(args, torch, dev, daq, synth, W)
-
-    # ---- served form: request loop with admission, overlap and resident Q
-    if not args.no_served and not args.quick:
-        result["served"] = bench_served(args, torch, dev, daq, synth, W, samples)
-
-    # ---- stress batch: 48 fills (69.67 GB) in one call, output sizes computed on the device
-    if not args.no_stress and not args.quick:
-        result["stress"] = bench_stress(args, torch, dev, daq, synth, W)
-
-    # ---- sparse regime: islands cover ~8% of the fill
-    if not args.no_sparse and not args.quick:
-        result["sparse"] = bench_sparse(args, torch, dev, daq, synth, W)
-
-    # ---- lossless packing of the pool rows
-    if not args.no_pack and not args.quick:
-        result["pack"] = bench_pack(args, torch, dev, daq, out.pool, n_rows)
-
-    # ---- per-crystal full-resolution fill sum
-    if not args.no_crystal_sum and not args.quick:
-        result["crystal_sum"] = bench_crystal_sum(args, torch, dev, daq, samples)
-
-    # ---- island-finding efficiency across thresholds (Fig. 2)
-    if not args.no_threshold_scan and not args.quick and rank == 0:
-        scan = threshold_scan(torch, dev, daq, synth, W)
-        result["threshold_scan"] = {"datasets": scan["datasets"],
-                                    "slope": {t: v["slope"] for t, v in scan["thresholds"].items()},
-                                    "corr": {t: v["corr"] for t, v in scan["thresholds"].items()},
-                                    "ratio_of_totals": {t: v["ratio_of_totals"] for t, v in scan["thresholds"].items()}}
-
-    # ---- plain form: one CTA per tile, no persistence
-    if not args.quick:
-        pp, _ = make_p(grid=-1)
-        pp.workspace, pp.workspace_bytes = workspace.data_ptr(), wsb
-        Kp = max(3, min(K, 200))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            for _ in range(3):
-                call(pp)
-            e0.record(stream)
-            for _ in range(Kp):
-                call(pp)
-            e1.record(stream)
-        torch.cuda.synchronize(dev)
-        result["plain_form"] = {"value": round(Kp * raw_bytes / (e0.elapsed_time(e1) * 1e-3) / 1e9, 2),
-                                "unit": UNIT, "steps": Kp, "form": "single-pass plain kernel, one CTA per tile"}
-
-    # ---- end to end through the host-buffer entry point
+    # ---- end to end through the host-buffer entry point (before the sections that fill device memory)
     if not args.no_e2e:
         hdr_h = torch.empty(out.hdr_cap * 3, dtype=torch.int64).pin_memory()
         pool_h = torch.empty((rows_cap, X), dtype=torch.int16).pin_memory()
@@ -423,6 +374,55 @@ def bench_gb300(args, ws, rank, local):
                                     "h2d_bytes_per_step": raw_bytes, "d2h_bytes_per_step": pk_d2h,
                                     "api": "daq_process_fills_host with DAQ_PACK_POOL (pool rows packed losslessly "
                                            "on the GPU before the copy back)"}}
+
+    # ---- batched form: 16 uneven fills in one tuned, graph-captured launch
+    if not args.no_batched and not args.quick:
+        result["batched"] = bench_batched(args, torch, dev, daq, synth, W)
+
+    # ---- served form: request loop with admission, overlap and resident Q
+    if not args.no_served and not args.quick:
+        result["served"] = bench_served(args, torch, dev, daq, synth, W, samples)
+
+    # ---- stress batch: 48 fills (69.67 GB) in one call, output sizes computed on the device
+    if not args.no_stress and not args.quick:
+        result["stress"] = bench_stress(args, torch, dev, daq, synth, W)
+
+    # ---- sparse regime: islands cover ~8% of the fill
+    if not args.no_sparse and not args.quick:
+        result["sparse"] = bench_sparse(args, torch, dev, daq, synth, W)
+
+    # ---- lossless packing of the pool rows
+    if not args.no_pack and not args.quick:
+        result["pack"] = bench_pack(args, torch, dev, daq, out.pool, n_rows)
+
+    # ---- per-crystal full-resolution fill sum
+    if not args.no_crystal_sum and not args.quick:
+        result["crystal_sum"] = bench_crystal_sum(args, torch, dev, daq, samples)
+
+    # ---- island-finding efficiency across thresholds (Fig. 2)
+    if not args.no_threshold_scan and not args.quick and rank == 0:
+        scan = threshold_scan(torch, dev, daq, synth, W)
+        result["threshold_scan"] = {"datasets": scan["datasets"],
+                                    "slope": {t: v["slope"] for t, v in scan["thresholds"].items()},
+                                    "corr": {t: v["corr"] for t, v in scan["thresholds"].items()},
+                                    "ratio_of_totals": {t: v["ratio_of_totals"] for t, v in scan["thresholds"].items()}}
+
+    # ---- plain form: one CTA per tile, no persistence
+    if not args.quick:
+        pp, _ = make_p(grid=-1)
+        pp.workspace, pp.workspace_bytes = workspace.data_ptr(), wsb
+        Kp = max(3, min(K, 200))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                call(pp)
+            e0.record(stream)
+            for _ in range(Kp):
+                call(pp)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        result["plain_form"] = {"value": round(Kp * raw_bytes / (e0.elapsed_time(e1) * 1e-3) / 1e9, 2),
+                                "unit": UNIT, "steps": Kp, "form": "single-pass plain kernel, one CTA per tile"}
 
     # ---- CPU baseline: the oracle on a bounded sample of the same fill (rank 0)
     if rank == 0 and not args.no_cpu_baseline:
