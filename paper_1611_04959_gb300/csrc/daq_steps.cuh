@@ -188,8 +188,11 @@ __device__ __forceinline__ bool aborted(const KArgs &a)
 // Map a ticket to its tile.  Tiles are numbered fill by fill, calorimeter by
 // calorimeter, then in time; a fill of length len has ceil(len / TW) tiles
 // per calorimeter.
+// want_ptot = false leaves T.ptot at 0 (no global load; for callers that
+// issue a bulk copy right after decoding and take the pedestal sum elsewhere).
 template <int TW>
-__device__ bool decode_tile(const KArgs &a, long long tile, TileInfo &T, const long long *fts, const int32_t *lens)
+__device__ bool decode_tile(const KArgs &a, long long tile, TileInfo &T, const long long *fts, const int32_t *lens,
+                            bool want_ptot = true)
 {
     const long long total = fts[a.n_fills];
     T.tile = -1;
@@ -208,7 +211,7 @@ __device__ bool decode_tile(const KArgs &a, long long tile, TileInfo &T, const l
     T.t0 = (rem % tpc) * TW;
     T.len = len;
     T.t_end = T.t0 + TW < len ? T.t0 + TW : len;
-    T.ptot = a.ptot[(long long)lo * a.n_calo + T.c];
+    T.ptot = want_ptot ? a.ptot[(long long)lo * a.n_calo + T.c] : 0;
     T.pad = 0;
     return true;
 }

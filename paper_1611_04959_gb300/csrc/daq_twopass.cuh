@@ -186,6 +186,7 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
 
     for (int i = tid; i < 32 * NS; i += kThr) reinterpret_cast<uint32_t *>(abyte0)[i] = 0u;
     const PlanView plan = cache_plan(a, fts_s, lens_s, tid, kThr);
+
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(full + s, 1);
@@ -543,7 +544,9 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
         return boxes;
     };
     auto start_load = [&](long long tile, uint32_t boxes) {  // one thread
-        decode_tile<TW>(a, tile, *tinfo, plan.fts, plan.lens);
+        // no pedestal sum: the compact pass does not use it, and its load would
+        // delay the bulk copy
+        decode_tile<TW>(a, tile, *tinfo, plan.fts, plan.lens, false);
         trace_stamp(a, tile, 5);
         if (a.use_tma) {
             fence_proxy_async_smem();
