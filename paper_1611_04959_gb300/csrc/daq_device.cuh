@@ -175,6 +175,12 @@ __device__ __forceinline__ void tma_load_2d_hint(void *dst, const void *tmap, in
         : "memory");
 }
 
+// Programmatic dependent launch: wait until the preceding kernel of the stream
+// has completed and its memory is visible (a no-op for a kernel launched
+// without the attribute), and let the following kernel be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ void ld_relaxed_b128(const void *p, unsigned long long &lo, unsigned long long &hi)
 {
     asm volatile(

@@ -99,6 +99,7 @@ __device__ __forceinline__ long long floor_div_ll(long long a, long long b)
 // tile-status array.
 __global__ void __launch_bounds__(kThreads) daq_prepare_kernel(KArgs a, int tw)
 {
+    pdl_trigger();  // the count kernel's CTAs may become resident; they wait for this kernel to finish
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __shared__ long long s_warp[kWarps];
     __shared__ long long s_carry;
@@ -911,6 +912,25 @@ template <int TW> static cudaError_t launch_pipe(const KArgs &a, const Plan &pl,
     return cudaGetLastError();
 }
 
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// while the previous kernel of the stream drains; it waits for it in-kernel
+// (pdl_wait) before reading its outputs.
+template <typename K>
+static cudaError_t launch_pdl(K kernel, int grid, int block, size_t smem, cudaStream_t s, const KArgs &a)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 // Count pass, scan, compact pass.  Events (optional): [2] after the count
 // kernel, [3] after the scan, [4] after the compact kernel.
 template <int TW>
@@ -940,18 +960,14 @@ static cudaError_t launch_twopass(const KArgs &a, const Plan &pl, int grid, int 
     }
     grid_a = (int)std::min<int64_t>(grid_a, tiles);
     grid_b = (int)std::min<int64_t>(grid_b, tiles);
-    if (ns3) daq_count_kernel<TW, 3><<<grid_a, count_thr, pl.smem, s>>>(a);
-    else daq_count_kernel<TW, 2><<<grid_a, count_thr, pl.smem, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = ns3 ? launch_pdl(daq_count_kernel<TW, 3>, grid_a, count_thr, pl.smem, s, a)
+            : launch_pdl(daq_count_kernel<TW, 2>, grid_a, count_thr, pl.smem, s, a);
+    if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
     const int scan_blocks = (int)((tiles + kScanChunk - 1) / kScanChunk);
-    daq_scan_kernel<<<scan_blocks, kScanThreads, 0, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_pdl(daq_scan_kernel, scan_blocks, kScanThreads, 0, s, a)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
-    if (!skip_isl) {
-        daq_compact_kernel<TW><<<grid_b, 256, pl.smem_b, s>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    if (!skip_isl && (e = launch_pdl(daq_compact_kernel<TW>, grid_b, 256, pl.smem_b, s, a)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[4], s)) != cudaSuccess) return e;
     return cudaSuccess;
 }

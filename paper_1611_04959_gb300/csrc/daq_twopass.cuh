@@ -319,6 +319,8 @@ template <int TW, int NS>
 __global__ void __launch_bounds__(count_threads<NS>(), NS == 2 ? 2 : 1) daq_count_kernel(const __grid_constant__ KArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
+    pdl_wait();     // the prepare kernel's plan, pedestals and resets
+    pdl_trigger();  // the scan may be scheduled as CTAs finish
     count_role<TW, false, NS>(a, smem, blockIdx.x, gridDim.x);
 }
 
@@ -367,6 +369,8 @@ __device__ __forceinline__ Agg block_scan_incl(Agg v, Agg *warp_tot, Agg *block_
 // writes every tile's exclusive prefix.
 __global__ void __launch_bounds__(kScanThreads) daq_scan_kernel(const __grid_constant__ KArgs a)
 {
+    pdl_wait();  // every tile's record
+    pdl_trigger();
     __shared__ Agg warp_tot[kScanThreads / 32];
     __shared__ Agg s_incl[kScanThreads];
     __shared__ Agg s_prefix;
@@ -677,6 +681,7 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
 template <int TW>
 __global__ void __launch_bounds__(256, 2) daq_compact_kernel(const __grid_constant__ KArgs a)
 {
+    pdl_wait();  // every tile's prefix
     extern __shared__ __align__(128) unsigned char smem[];
     compact_role<TW, false>(a, smem, blockIdx.x, gridDim.x);
 }
