@@ -926,8 +926,10 @@ static cudaError_t launch_pdl(K kernel, int grid, int block, size_t smem, cudaSt
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return cudaErrorUnknown;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = cap == cudaStreamCaptureStatusNone ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
