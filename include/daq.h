@@ -85,9 +85,14 @@ typedef struct daq_island {
  *                NULL for n_samples each.  Out-of-range values are clamped and
  *                flagged with DAQ_DEV_BAD_FILL_LEN.
  *   flags        DAQ_SKIP_Q | DAQ_SKIP_ISLANDS | DAQ_SYNC.
- *   tile         largest samples per tile to use: 0 = 448; else 128, 224, 448 or
- *                960.  The call takes the largest supported width not above it
- *                whose shared-memory plan fits (960 only for the plain kernel).
+ *   tile         samples per tile: 0 = chosen by the library (two-pass form: the
+ *                width of least estimated count-pass cost, 448 for the nominal
+ *                windows and 384 when the halo of post + pre samples is too
+ *                wide for two count CTAs per SM at 448; other forms: 448);
+ *                else the largest width not above 128, 224, 384, 448 or 960
+ *                that this form supports and whose shared-memory plan fits
+ *                (384 only for the two-pass form, 960 only for the plain
+ *                kernel).
  *   grid         0  = two-pass form (count kernel, scan, compact kernel), grids
  *                     from occupancy (default);
  *                > 0 = two-pass form with exactly this many CTAs per kernel;
@@ -324,11 +329,11 @@ int daq_process_fills_static(const int16_t *samples, int n_calo, int n_xtal, int
  *                plan then allocates and owns one.  With DAQ_TUNE, params->tile
  *                and params->grid are ignored and chosen by the tuner.
  *   plan_flags   DAQ_TUNE: time the candidate configurations (two-pass form at
- *                tile widths 128/224/448 with 2 or 1 CTAs per SM; the
- *                single-pass forms) on this batch and keep the fastest.  The
- *                choice is remembered per (device, sizes, windows, decimation,
- *                flags) for the rest of the process.  DAQ_TUNE_FORCE: ignore a
- *                remembered choice.
+ *                the library's tile and at tile widths 128/224/384/448 with 2 or
+ *                1 CTAs per SM; the single-pass forms) on this batch and keep
+ *                the fastest.  The choice is remembered per (device, sizes,
+ *                windows, decimation, flags) for the rest of the process.
+ *                DAQ_TUNE_FORCE: ignore a remembered choice.
  *   *plan        receives the plan (NULL on error).
  * Creation is not the hot call: it may allocate, synchronises the device, and
  * runs the batch several times (tuning and a warm-up run) with islands_out as
@@ -353,7 +358,7 @@ typedef struct daq_tune_result {
     int32_t n_tried;   /* candidates timed (0 if not tuned or taken from the cache) */
     int32_t from_cache;
     float ms;          /* mean time per run of the chosen candidate (ms), 0 if not timed */
-    float ms_default;  /* the same for the default configuration (tile 448, grid 0) */
+    float ms_default;  /* the same for the default configuration (tile 0, grid 0) */
 } daq_tune_result;
 
 int daq_batch_plan_create(const int16_t *samples, int n_calo, int n_xtal, int64_t n_samples, int n_fills,

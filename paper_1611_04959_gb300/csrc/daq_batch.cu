@@ -52,13 +52,14 @@ struct Candidate {
     int tile, grid;
 };
 
-// Form x tile x CTAs: two-pass at 128 / 224 / 448 with occupancy grids (2 CTAs
-// per SM) and with one CTA per SM; the single-launch form at 448 / 224; the
+// Form x tile x CTAs: the default (two-pass, tile chosen by the library), the
+// two-pass form at 128 / 224 / 384 / 448 with occupancy grids (2 CTAs per SM)
+// and with one CTA per SM; the single-launch form at 448 / 224; the
 // single-pass forms for comparison.
 std::vector<Candidate> candidates(int sms)
 {
-    return {{448, 0},  {224, 0},  {128, 0},  {448, sms}, {224, sms}, {448, -4},
-            {224, -4}, {448, -1}, {960, -1}, {448, -2},  {448, -3}};
+    return {{0, 0},      {448, 0},   {384, 0},  {224, 0},  {128, 0},  {448, sms}, {224, sms},
+            {448, -4},   {224, -4},  {448, -1}, {960, -1}, {448, -2}, {448, -3}};
 }
 
 int q_values(int64_t N, int C, const daq_params &p, int64_t *n)
@@ -217,7 +218,7 @@ int daq_batch_plan_create(const int16_t *samples, int n_calo, int n_xtal, int64_
             cudaEventElapsedTime(&ms, e0, e1);
             ms /= kReps;
             ++tried;
-            if (c.tile == 448 && c.grid == 0) pl->tune.ms_default = ms;
+            if (c.tile == 0 && c.grid == 0) pl->tune.ms_default = ms;
             if (best_ms < 0.f || ms < best_ms) {
                 best_ms = ms;
                 best = c;

@@ -829,6 +829,21 @@ static bool encode_tensor_map(CUtensorMap *m, const int16_t *samples, int64_t ro
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Estimated count-pass time per sample of a two-pass plan, relative to a tile
+// that loads no halo with two CTAs per SM: the columns each tile loads (tile,
+// halos and box rounding) per tile sample, times the cost of one CTA per SM.
+// The count kernel is bound by the bytes it keeps in flight; one CTA with
+// three slots ran 1.4x slower per loaded byte than two CTAs with two slots
+// each (full fill, post = 64: 0.377 ms at 448 samples with one CTA per SM).
+constexpr double kOneCountCtaCost = 1.4;
+
+static double count_cost(const Plan &pl)
+{
+    const double cols = (double)pl.nbox * pl.boxw / pl.tw;
+    const bool two_ctas = 2 * (pl.smem + kSmemPerBlockReserved) <= (size_t)kSmemPerSM;
+    return two_ctas ? cols : cols * kOneCountCtaCost;
+}
+
 static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, const daq_params *p, Plan *pl)
 {
     if (!p || n_calo < 0 || n_fills < 0 || n_samples < 0 || n_xtal < 1) return DAQ_EINVAL;
@@ -848,7 +863,8 @@ static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, con
         if (p->decim[d] < 1) return DAQ_EINVAL;
         if (p->decim[d] % 8) pl->need_sarr = 1;
     }
-    if (p->tile != 0 && p->tile != 128 && p->tile != 224 && p->tile != 448 && p->tile != 960) return DAQ_EINVAL;
+    if (p->tile != 0 && p->tile != 128 && p->tile != 224 && p->tile != 384 && p->tile != 448 && p->tile != 960)
+        return DAQ_EINVAL;
     pl->mode = p->grid >= 0    ? kModeTwoPass
                : p->grid == -3 ? kModePipelined
                : p->grid == -4 ? kModeFused
@@ -856,17 +872,31 @@ static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, con
                                : kModePlain;
     const int hl = (p->post + 1 + 7) & ~7, hr = (p->pre + 1 + 7) & ~7;
     const int limit = p->tile ? p->tile : 448;
+    // An explicit tile: the widest supported width not above it that fits.
+    // Two-pass form with tile 0: the width of least estimated count-pass cost
+    // (the slowest to fit wide halos).
+    const bool by_cost = p->tile == 0 && pl->mode == kModeTwoPass;
     int chosen = -1;
-    for (int tw : {960, 448, 224, 128}) {
+    double best = 0.0;
+    for (int tw : {960, 448, 384, 224, 128}) {
         if (tw > limit) continue;
         if (tw == 960 && pl->mode != kModePlain) continue;
+        if (tw == 384 && pl->mode != kModeTwoPass) continue;
         if (tw + hl + hr > kMaxExtBits) continue;
         plan_geometry(pl, tw, p->pre, p->post, n_xtal);
         if (pl->smem > (size_t)kSmemBudget || pl->smem_b > (size_t)kSmemBudget) continue;
-        chosen = tw;
-        break;
+        if (!by_cost) {
+            chosen = tw;
+            break;
+        }
+        const double cost = count_cost(*pl);
+        if (chosen < 0 || cost < best) {
+            chosen = tw;
+            best = cost;
+        }
     }
     if (chosen < 0) return DAQ_EUNSUPPORTED;
+    if (chosen != pl->tw) plan_geometry(pl, chosen, p->pre, p->post, n_xtal);
     pl->max_tiles = (int64_t)n_fills * n_calo * ((n_samples + chosen - 1) / chosen);
     return DAQ_OK;
 }
@@ -1217,6 +1247,7 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
         switch (pl.tw) {
         case 128: e = launch_twopass<128>(a, pl, p.grid, di.sms, skip_isl, ev, s); break;
         case 224: e = launch_twopass<224>(a, pl, p.grid, di.sms, skip_isl, ev, s); break;
+        case 384: e = launch_twopass<384>(a, pl, p.grid, di.sms, skip_isl, ev, s); break;
         default: e = launch_twopass<448>(a, pl, p.grid, di.sms, skip_isl, ev, s); break;
         }
     } else if (pl.mode == kModePipelined) {

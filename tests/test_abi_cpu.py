@@ -58,6 +58,21 @@ def test_host_calls(daq):
     assert daq.daq_status_from_counts([5, 5, daq.DAQ_DEV_TIMEOUT, 1]) == daq.DAQ_ETIMEOUT
 
 
+@pytest.mark.parametrize("pre,post,grid,tile,expect", [
+    (8, 24, 0, 0, 448),      # nominal windows: 448-sample tiles, two count CTAs per SM
+    (8, 64, 0, 0, 384),      # a 72-sample left halo: two CTAs fit only at 384
+    (8, 64, 0, 448, 448),    # an explicit tile is kept while its plan fits (one CTA per SM)
+    (8, 64, 0, 384, 384),
+    (8, 64, -4, 0, 448),     # other forms: 448 unless it does not fit
+    (8, 64, -4, 384, 224),   # 384 is a two-pass width only
+    (8, 24, 0, 384, 384),
+])
+def test_tile_choice(daq, pre, post, grid, tile, expect):
+    """The plan's tile width, read back through the tile count of a full fill."""
+    p = daq.make_params(threshold=15, pre=pre, post=post, decim=(8, 32), grid=grid, tile=tile)
+    assert daq.daq_trace_tiles(24, 54, 560_000, 1, p) == 24 * -(-560_000 // expect)
+
+
 @pytest.mark.parametrize("bad", [
     dict(pre=-1), dict(post=-2), dict(ped_samples=0), dict(decim=(0,)), dict(pre=300, post=300),
     dict(tile=100), dict(grid=-6), dict(lag_tiles=-1), dict(calo_base=-1), dict(q_calos=-1), dict(calo_base=1, q_calos=1),

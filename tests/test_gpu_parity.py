@@ -49,7 +49,7 @@ def test_plain_one_calorimeter_full_fill(env):
     assert ref["n_islands"] > 100
 
 
-@pytest.mark.parametrize("tile", [128, 224, 448, 960])
+@pytest.mark.parametrize("tile", [128, 224, 384, 448, 960])
 @pytest.mark.parametrize("grid", [0, -1, -2, -3, -4, -5, 1, 5])
 def test_tile_and_grid_invariance(env, tile, grid):
     from synth import workloads as W
@@ -80,7 +80,7 @@ def _random_case(rng):
     if rng.random() < 0.5:
         fill_len = rng.integers(0, N + 1, size=F).astype(np.int32)
         fill_len[rng.random(F) < 0.2] = N
-    tile = int(rng.choice([0, 128, 224, 448]))
+    tile = int(rng.choice([0, 128, 224, 384, 448]))
     return s, params, fill_len, tile
 
 
@@ -103,11 +103,14 @@ def test_uneven_batch_of_fills(env):
     compare(env, s, w.params(), fill_len=fl)
 
 
-def test_stress_parameters(env):
+@pytest.mark.parametrize("tile", [0, 384, 448])
+def test_stress_parameters(env, tile):
+    """post = 64: the default plan takes 384-sample tiles (two count CTAs per
+    SM); 448 runs one count CTA per SM with three tile slots."""
     from synth import workloads as W
     w = W.scaled(W.STRESS, n_fills=2, n_calo=3)
     s = env["synth"].generate(w.config())
-    res, ref = compare(env, s, w.params())
+    res, ref = compare(env, s, w.params(), tile=tile)
     assert ref["n_rows"] > 0.95 * s.shape[0] * s.shape[1] * s.shape[3]   # heavy merging
 
 
@@ -133,7 +136,8 @@ def test_empty_batch(env):
         assert res["n_islands"] == 0 and res["n_rows"] == 0
 
 
-def test_capacity_overflow_reports_sizes_and_keeps_prefix(env):
+@pytest.mark.parametrize("grid", [0, -4, -5])
+def test_capacity_overflow_reports_sizes_and_keeps_prefix(env, grid):
     torch, daq, oracle = env["torch"], env["daq"], env["oracle"]
     from synth import workloads as W
     w = W.scaled(W.PLAIN_FULL_FILL, n_calo=2, n_samples=30_000)
@@ -141,7 +145,7 @@ def test_capacity_overflow_reports_sizes_and_keeps_prefix(env):
     ref = oracle.process_fills(s, w.params())
     hc, pc = ref["n_islands"] // 3, ref["n_rows"] // 2
     q0 = torch.zeros(daq.q_size(2, 30_000, (32,)), dtype=torch.int64, device="cuda")
-    res = daq.process_fills(torch.from_numpy(s).cuda(), hdr_cap=hc, pool_cap=pc, q=q0, **w.params())
+    res = daq.process_fills(torch.from_numpy(s).cuda(), hdr_cap=hc, pool_cap=pc, q=q0, grid=grid, **w.params())
     assert res["status"] == daq.DAQ_ECAPACITY
     assert res["n_islands"] == ref["n_islands"] and res["n_rows"] == ref["n_rows"]
     assert res["counts"][2] & (daq.DAQ_DEV_HDR_OVERFLOW | daq.DAQ_DEV_POOL_OVERFLOW)
@@ -151,7 +155,8 @@ def test_capacity_overflow_reports_sizes_and_keeps_prefix(env):
     assert np.array_equal(q0.cpu().numpy(), ref["q"])          # Q is accumulated exactly once
 
 
-def test_q_accumulates_across_calls_and_skip_flags(env):
+@pytest.mark.parametrize("grid", [0, -4, -5])
+def test_q_accumulates_across_calls_and_skip_flags(env, grid):
     torch, daq, oracle = env["torch"], env["daq"], env["oracle"]
     from synth import workloads as W
     w = W.scaled(W.STRESS, n_fills=1, n_calo=2, n_samples=50_000)
@@ -159,9 +164,9 @@ def test_q_accumulates_across_calls_and_skip_flags(env):
     ref = oracle.process_fills(s, w.params())
     ds = torch.from_numpy(s).cuda()
     q = torch.zeros(daq.q_size(2, 50_000, (8, 32)), dtype=torch.int64, device="cuda")
-    daq.process_fills(ds, q=q, **w.params())
-    daq.process_fills(ds, q=q, flags=daq.DAQ_SKIP_ISLANDS, **w.params())
-    r3 = daq.process_fills(ds, q=q, flags=daq.DAQ_SKIP_Q, **w.params())
+    daq.process_fills(ds, q=q, grid=grid, **w.params())
+    daq.process_fills(ds, q=q, flags=daq.DAQ_SKIP_ISLANDS, grid=grid, **w.params())
+    r3 = daq.process_fills(ds, q=q, flags=daq.DAQ_SKIP_Q, grid=grid, **w.params())
     assert np.array_equal(q.cpu().numpy(), 2 * ref["q"])
     assert r3["n_islands"] == ref["n_islands"]
 
