@@ -552,9 +552,10 @@ int daq_crystal_sum(const int16_t *samples, int n_calo, int n_xtal, int64_t n_sa
  *            bit k of z_i).
  * daq_pack_bound          worst-case stream bytes for rows x n_xtal (-1 if invalid).
  * daq_pack_workspace_size device scratch daq_pack_pool needs.
- * daq_pack_pool           pack device pool[rows][n_xtal] (n_xtal <= 64) into
- *                         device out (16-byte aligned, out_cap bytes) on
- *                         `stream`; *out_bytes (device int64) receives the
+ * daq_pack_pool           pack device pool[rows][n_xtal] (n_xtal <= 64,
+ *                         16-byte aligned) into device out (16-byte aligned,
+ *                         out_cap bytes) on `stream`; *out_bytes (device
+ *                         int64) receives the
  *                         stream's size - bytes past out_cap are not written,
  *                         so out_cap >= daq_pack_bound() is always enough.
  * daq_unpack_pool         decode a stream of in_bytes bytes into device

@@ -15,10 +15,14 @@
 // One warp per block: the block's rows are copied to shared memory (row pitch
 // an odd number of words, so a warp reading one crystal down 32 rows hits 32
 // banks), each crystal column's differences are formed with one shuffle, its
-// width with one max-reduction and its planes with one ballot each.  A size
-// pass, an exclusive scan of the block sizes (three kernels) and a write pass;
-// the decoder is the same walk backwards (ballots become bit extraction, the
-// differences an inclusive warp scan).
+// width with one OR-reduction (the bit length of the OR of the z_i is that of
+// their maximum) and its planes with one ballot each.  A size pass (which also
+// keeps every crystal column's width), an exclusive scan of the block sizes
+// (three kernels) and a write pass that reads the widths back; the decoder is
+// the same walk backwards (ballots become bit extraction, the differences an
+// inclusive warp scan).  (A single pass whose warps found their block's place
+// by decoupled look-back was 2.3x slower: with thousands of one-block warps in
+// flight the nearest published prefix lies hundreds of blocks back.)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,7 +40,7 @@ constexpr uint32_t kMagic = 0x50514144u;
 constexpr int kScanPer = 4;
 constexpr int kScanChunk = kThreads * kScanPer;
 
-__device__ __forceinline__ uint32_t zigzag(int32_t d) { return d >= 0 ? 2u * (uint32_t)d : 2u * (uint32_t)(-d) - 1u; }
+__device__ __forceinline__ uint32_t zigzag(int32_t d) { return ((uint32_t)d << 1) ^ (uint32_t)(d >> 31); }
 
 __device__ __forceinline__ int32_t unzigzag(uint32_t z) { return (z & 1u) ? -(int32_t)((z + 1u) >> 1) : (int32_t)(z >> 1); }
 
@@ -64,24 +68,31 @@ __device__ __forceinline__ int load_block(const int16_t *pool, long long rows, i
     return nv;
 }
 
+// Block sizes, and the width of every crystal column (widths[b][x]).
 __global__ void __launch_bounds__(kThreads) pack_size_kernel(const int16_t *pool, long long rows, int X,
-                                                             long long nb, unsigned long long *sizes)
+                                                             long long nb, unsigned long long *sizes,
+                                                             uint8_t *widths)
 {
     __shared__ __align__(16) int16_t sm_all[kWarps][kBlockElems];
+    __shared__ uint8_t w_all[kWarps][kMaxX];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int16_t *sm = sm_all[warp];
-    const int P = X;
+    uint8_t *wsm = w_all[warp];
+    const int16_t *row = sm + lane * X;
     for (long long b = (long long)blockIdx.x * kWarps + warp; b < nb; b += (long long)gridDim.x * kWarps) {
         load_block(pool, rows, X, b, sm, lane);
         unsigned words = 0;
         for (int x = 0; x < X; ++x) {
-            const int32_t v = sm[lane * P + x];
-            const int32_t prev = __shfl_up_sync(kFull, v, 1);
-            const uint32_t z = lane ? zigzag(v - prev) : 0u;
-            const uint32_t m = __reduce_max_sync(kFull, z);
-            words += 1u + (m ? 32u - __clz(m) : 0u);
+            const int32_t v = row[x];
+            const uint32_t z = zigzag(v - __shfl_up_sync(kFull, v, 1));  // lane 0: its own value, z = 0
+            const uint32_t m = __reduce_or_sync(kFull, z);
+            const int w = m ? 32 - __clz(m) : 0;
+            wsm[x] = (uint8_t)w;  // every lane: the same byte
+            words += 1u + (unsigned)w;
         }
         if (lane == 0) sizes[b] = 4ull * words;
+        __syncwarp();
+        for (int x = lane; x < X; x += 32) widths[b * X + x] = wsm[x];
         __syncwarp();
     }
 }
@@ -173,39 +184,77 @@ __global__ void __launch_bounds__(kThreads) scan_apply_kernel(const unsigned lon
     }
 }
 
+// 32 x 32 bit transpose across the warp: lane j receives bit j of every lane's
+// x (bit i of the result = bit j of lane i's x).  Five stages of the recursive
+// block swap: at stage s the lane pairs (l, l ^ s) exchange the off-diagonal
+// s x s blocks - the lane with bit s clear keeps the bits whose index has bit
+// s clear (mask m) and takes its partner's such bits shifted up by s, the
+// other keeps ~m and takes its partner's ~m bits shifted down by s.  Each
+// shift is a rotation (funnel shift) whose unwanted bits the select drops, so
+// a stage is one shuffle, one rotation and one bitwise select.
+struct Transpose {
+    uint32_t keep[5];
+    int rot[5];
+    __device__ __forceinline__ explicit Transpose(int lane)
+    {
+        constexpr uint32_t kMask[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            const int sft = 16 >> t;
+            const bool low = (lane & sft) == 0;
+            keep[t] = low ? kMask[t] : ~kMask[t];
+            rot[t] = low ? sft : 32 - sft;
+        }
+    }
+    __device__ __forceinline__ uint32_t operator()(uint32_t x) const
+    {
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            const uint32_t y = __shfl_xor_sync(kFull, x, 16 >> t);
+            const uint32_t r = __funnelshift_l(y, y, rot[t]);
+            x = (x & keep[t]) | (r & ~keep[t]);
+        }
+        return x;
+    }
+};
+
+// Lane k + 1 holds bit plane k of the column (the transpose of z << 1, so bit
+// k of z is bit k + 1 of the transposed row), lane 0 the head word; lanes
+// 0 .. w store the column's 1 + w words with one coalesced store.
 __global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *pool, long long rows, int X, long long nb,
-                                                              const unsigned long long *offs, unsigned char *out,
-                                                              long long cap)
+                                                              const unsigned long long *offs, const uint8_t *widths,
+                                                              unsigned char *out, long long cap)
 {
     __shared__ __align__(16) int16_t sm_all[kWarps][kBlockElems];
+    __shared__ uint8_t w_all[kWarps][kMaxX];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int16_t *sm = sm_all[warp];
-    const int P = X;
+    uint8_t *wsm = w_all[warp];
+    const int16_t *row = sm + lane * X;
+    const Transpose transpose(lane);
+    uint32_t *out32 = reinterpret_cast<uint32_t *>(out);
     const long long head = 16 + 8 * (nb + 1);
     if (blockIdx.x == 0 && threadIdx.x == 0 && cap >= 16) {
-        uint32_t *h = reinterpret_cast<uint32_t *>(out);
-        h[0] = kMagic;
-        h[1] = (uint32_t)X;
+        out32[0] = kMagic;
+        out32[1] = (uint32_t)X;
         reinterpret_cast<unsigned long long *>(out)[1] = (unsigned long long)rows;
     }
     for (long long b = (long long)blockIdx.x * kWarps + warp; b < nb; b += (long long)gridDim.x * kWarps) {
-        load_block(pool, rows, X, b, sm, lane);
-        long long pos = head + (long long)offs[b];  // bytes, a multiple of 4
+        for (int x = lane; x < X; x += 32) wsm[x] = widths[b * X + x];
+        load_block(pool, rows, X, b, sm, lane);  // ends with __syncwarp
+        const long long start = head + (long long)offs[b];  // bytes, a multiple of 4
+        uint32_t *dst = out32 + (start >> 2);
+        // bytes that may be written from the block's start (a block is < 2^13 bytes)
+        const int room = (int)max(0ll, min(cap - start, 1ll << 20));
+        int o = 0;  // words of the block written so far
         for (int x = 0; x < X; ++x) {
-            const int32_t v = sm[lane * P + x];
-            const int32_t prev = __shfl_up_sync(kFull, v, 1);
-            const uint32_t z = lane ? zigzag(v - prev) : 0u;
-            const uint32_t m = __reduce_max_sync(kFull, z);
-            const int w = m ? 32 - __clz(m) : 0;
-            const int32_t v0 = __shfl_sync(kFull, v, 0);
-            uint32_t mine = (uint32_t)(uint16_t)v0 | ((uint32_t)w << 16);  // lane 0: head word
-            for (int k = 0; k < w; ++k) {
-                const uint32_t plane = __ballot_sync(kFull, (z >> k) & 1u);
-                if (lane == k + 1) mine = plane;
-            }
-            if (lane <= w && pos + 4ll * lane + 4 <= cap)
-                reinterpret_cast<uint32_t *>(out + pos)[lane] = mine;
-            pos += 4ll * (1 + w);
+            const int32_t v = row[x];
+            const uint32_t z = zigzag(v - __shfl_up_sync(kFull, v, 1));
+            const int w = wsm[x];
+            const uint32_t planes = transpose(z << 1);
+            const uint32_t word = lane ? planes : ((uint32_t)(uint16_t)v | ((uint32_t)w << 16));
+            if (lane <= w && 4 * (o + lane) + 4 <= room) dst[o + lane] = word;
+            o += 1 + w;
         }
         __syncwarp();
     }
@@ -288,10 +337,10 @@ int grid_blocks(long long nb)
 }
 
 struct PackWs {
-    size_t sizes, offs, chunk, total;
+    size_t sizes, offs, chunk, widths, total;
 };
 
-PackWs pack_ws(long long nb)
+PackWs pack_ws(long long nb, int X)
 {
     auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
     PackWs w;
@@ -299,7 +348,8 @@ PackWs pack_ws(long long nb)
     w.offs = up(8 * (size_t)std::max<long long>(nb, 1));
     w.chunk = up(w.offs + 8 * (size_t)(nb + 1));
     const long long n_chunks = (nb + kScanChunk - 1) / kScanChunk;
-    w.total = up(w.chunk + 8 * (size_t)(n_chunks + 1));
+    w.widths = up(w.chunk + 8 * (size_t)(n_chunks + 1));
+    w.total = up(w.widths + (size_t)std::max<long long>(nb, 1) * (size_t)X);
     return w;
 }
 
@@ -319,7 +369,7 @@ int64_t daq_pack_bound(int64_t rows, int n_xtal)
 int daq_pack_workspace_size(int64_t rows, int n_xtal, size_t *bytes)
 {
     if (!bytes || rows < 0 || n_xtal < 1 || n_xtal > kMaxX) return DAQ_EINVAL;
-    *bytes = pack_ws((rows + 31) / 32).total;
+    *bytes = pack_ws((rows + 31) / 32, n_xtal).total;
     return DAQ_OK;
 }
 
@@ -328,26 +378,28 @@ int daq_pack_pool(const int16_t *pool, int64_t rows, int n_xtal, void *out, int6
 {
     if (rows < 0 || n_xtal < 1 || out_cap < 0 || !out_bytes || (rows > 0 && !pool)) return DAQ_EINVAL;
     if (n_xtal > kMaxX) return DAQ_EUNSUPPORTED;
-    if ((out_cap > 0 && !out) || (reinterpret_cast<uintptr_t>(out) & 15) || (reinterpret_cast<uintptr_t>(out_bytes) & 7))
+    if ((out_cap > 0 && !out) || (reinterpret_cast<uintptr_t>(out) & 15) || (reinterpret_cast<uintptr_t>(out_bytes) & 7) ||
+        (reinterpret_cast<uintptr_t>(pool) & 15))
         return DAQ_EINVAL;
     const long long nb = (rows + 31) / 32;
-    const PackWs w = pack_ws(nb);
+    const PackWs w = pack_ws(nb, n_xtal);
     if (!workspace || workspace_bytes < w.total || (reinterpret_cast<uintptr_t>(workspace) & 15)) return DAQ_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char *ws = static_cast<unsigned char *>(workspace);
     auto *sizes = reinterpret_cast<unsigned long long *>(ws + w.sizes);
     auto *offs = reinterpret_cast<unsigned long long *>(ws + w.offs);
     auto *chunk = reinterpret_cast<unsigned long long *>(ws + w.chunk);
+    auto *widths = reinterpret_cast<uint8_t *>(ws + w.widths);
     unsigned char *o = static_cast<unsigned char *>(out);
     const long long n_apply = nb / kScanChunk + 1;  // blocks covering entries 0..nb
-    if (nb > 0) pack_size_kernel<<<grid_blocks(nb), kThreads, 0, s>>>(pool, rows, n_xtal, nb, sizes);
+    if (nb > 0) pack_size_kernel<<<grid_blocks(nb), kThreads, 0, s>>>(pool, rows, n_xtal, nb, sizes, widths);
     if (nb > 0) scan_reduce_kernel<<<(unsigned)((nb + kScanChunk - 1) / kScanChunk), kThreads, 0, s>>>(sizes, nb, chunk);
     else if (cudaMemsetAsync(chunk, 0, 8, s) != cudaSuccess) return DAQ_ECUDA;
     scan_top_kernel<<<1, 1024, 0, s>>>(chunk, nb > 0 ? (nb + kScanChunk - 1) / kScanChunk : 0);
     scan_apply_kernel<<<(unsigned)n_apply, kThreads, 0, s>>>(sizes, nb, chunk, offs, o, out_cap,
                                                              reinterpret_cast<long long *>(out_bytes));
-    pack_write_kernel<<<grid_blocks(std::max<long long>(nb, 1)), kThreads, 0, s>>>(pool, rows, n_xtal, nb, offs, o,
-                                                                                   out_cap);
+    pack_write_kernel<<<grid_blocks(std::max<long long>(nb, 1)), kThreads, 0, s>>>(pool, rows, n_xtal, nb, offs,
+                                                                                   widths, o, out_cap);
     return cudaGetLastError() == cudaSuccess ? DAQ_OK : DAQ_ECUDA;
 }
 
