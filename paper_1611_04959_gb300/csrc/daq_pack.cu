@@ -16,13 +16,16 @@
 // an odd number of words, so a warp reading one crystal down 32 rows hits 32
 // banks), each crystal column's differences are formed with one shuffle, its
 // width with one OR-reduction (the bit length of the OR of the z_i is that of
-// their maximum) and its planes with one ballot each.  A size pass (which also
-// keeps every crystal column's width), an exclusive scan of the block sizes
-// (three kernels) and a write pass that reads the widths back; the decoder is
-// the same walk backwards (ballots become bit extraction, the differences an
-// inclusive warp scan).  (A single pass whose warps found their block's place
-// by decoupled look-back was 2.3x slower: with thousands of one-block warps in
-// flight the nearest published prefix lies hundreds of blocks back.)
+// their maximum) and its bit planes with one 32 x 32 bit transpose across the
+// warp, after which the lanes hold the planes in stream order.  A size pass
+// (which also keeps every crystal column's width), an exclusive scan of the
+// block sizes (three kernels) and a write pass that reads the widths back; the
+// decoder is the same walk backwards (one load of a column's words, the
+// transpose, the differences summed by an inclusive warp scan).  (One ballot
+// per plane, the first form, took 1.5x as long: the integer pipe ran out.  A
+// single pass whose warps found their block's place by decoupled look-back was
+// 2.3x slower: with thousands of one-block warps in flight the nearest
+// published prefix lies hundreds of blocks back.)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -218,9 +221,13 @@ struct Transpose {
     }
 };
 
-// Lane k + 1 holds bit plane k of the column (the transpose of z << 1, so bit
-// k of z is bit k + 1 of the transposed row), lane 0 the head word; lanes
-// 0 .. w store the column's 1 + w words with one coalesced store.
+// Crystal columns in pairs (a, b) whenever both widths are <= 16: one
+// transpose of z_a | z_b << 16 puts plane k of a in lane k and plane k of b
+// in lane 16 + k; one store writes both columns' planes, a second the two head
+// words (lane 0 from its own v_a, lane 1 from v_b of row 0, which the
+// difference shuffle brought it).  A column of width 17 (a difference of at
+// least 2^15) goes alone: lane k + 1 of the transposed z << 1 holds plane k,
+// lane 0 the head word.
 __global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *pool, long long rows, int X, long long nb,
                                                               const unsigned long long *offs, const uint8_t *widths,
                                                               unsigned char *out, long long cap)
@@ -232,6 +239,8 @@ __global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *poo
     uint8_t *wsm = w_all[warp];
     const int16_t *row = sm + lane * X;
     const Transpose transpose(lane);
+    const int kl = lane & 15;
+    const bool hi = lane >= 16;
     uint32_t *out32 = reinterpret_cast<uint32_t *>(out);
     const long long head = 16 + 8 * (nb + 1);
     if (blockIdx.x == 0 && threadIdx.x == 0 && cap >= 16) {
@@ -244,18 +253,41 @@ __global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *poo
         load_block(pool, rows, X, b, sm, lane);  // ends with __syncwarp
         const long long start = head + (long long)offs[b];  // bytes, a multiple of 4
         uint32_t *dst = out32 + (start >> 2);
-        // bytes that may be written from the block's start (a block is < 2^13 bytes)
-        const int room = (int)max(0ll, min(cap - start, 1ll << 20));
+        // words that may be written from the block's start (a block is < 2^11 words)
+        const int room = (int)(max(0ll, min(cap - start, 1ll << 20)) >> 2);
         int o = 0;  // words of the block written so far
-        for (int x = 0; x < X; ++x) {
+        auto single = [&](int x) {
             const int32_t v = row[x];
             const uint32_t z = zigzag(v - __shfl_up_sync(kFull, v, 1));
             const int w = wsm[x];
             const uint32_t planes = transpose(z << 1);
             const uint32_t word = lane ? planes : ((uint32_t)(uint16_t)v | ((uint32_t)w << 16));
-            if (lane <= w && 4 * (o + lane) + 4 <= room) dst[o + lane] = word;
+            if (lane <= w && o + lane < room) dst[o + lane] = word;
             o += 1 + w;
+        };
+        int x = 0;
+        for (; x + 1 < X; x += 2) {
+            const int wa = wsm[x], wb = wsm[x + 1];
+            if (max(wa, wb) > 16) {
+                single(x);
+                single(x + 1);
+                continue;
+            }
+            const int32_t va = row[x], vb = row[x + 1];
+            const int32_t pa = __shfl_up_sync(kFull, va, 1), pb = __shfl_up_sync(kFull, vb, 1);
+            const uint32_t za = zigzag(va - pa), zb = zigzag(vb - pb);
+            const uint32_t planes = transpose(za | (zb << 16));
+            const int ip = o + 1 + kl + (hi ? 1 + wa : 0);  // word of this lane's plane
+            if (kl < (hi ? wb : wa) && ip < room) dst[ip] = planes;
+            if (lane < 2) {
+                const int ih = lane ? o + 1 + wa : o;
+                const uint32_t hw = lane ? ((uint32_t)(uint16_t)pb | ((uint32_t)wb << 16))
+                                         : ((uint32_t)(uint16_t)va | ((uint32_t)wa << 16));
+                if (ih < room) dst[ih] = hw;
+            }
+            o += 2 + wa + wb;
         }
+        if (x < X) single(x);
         __syncwarp();
     }
 }
@@ -267,6 +299,7 @@ __global__ void __launch_bounds__(kThreads) unpack_kernel(const unsigned char *i
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int16_t *sm = sm_all[warp];
     const int P = X;
+    const Transpose transpose(lane);
     const long long head = 16 + 8 * (nb + 1);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const uint32_t *h = reinterpret_cast<const uint32_t *>(in);
@@ -283,21 +316,19 @@ __global__ void __launch_bounds__(kThreads) unpack_kernel(const unsigned char *i
         const unsigned long long off = offs[b];
         bool bad = off > (unsigned long long)(in_bytes - head) || (off & 3ull);
         long long pos = head + (long long)(bad ? 0ull : off);  // bytes read so far end at pos
-        const uint32_t *p = reinterpret_cast<const uint32_t *>(in + pos);
         for (int x = 0; x < X && !bad; ++x) {
-            if (pos + 4 > in_bytes) {
-                bad = true;
-                break;
-            }
-            const uint32_t h = p[0];
+            // the column's head word and planes: one load of up to 18 words
+            const uint32_t *p = reinterpret_cast<const uint32_t *>(in + pos);
+            const uint32_t q = lane < 18 && pos + 4ll * lane + 4 <= in_bytes ? p[lane] : 0u;
+            const uint32_t h = __shfl_sync(kFull, q, 0);
             const int w = (int)(h >> 16);
-            if (w > 17 || pos + 4ll * (1 + w) > in_bytes) {
+            if (pos + 4 > in_bytes || w > 17 || pos + 4ll * (1 + w) > in_bytes) {
                 bad = true;
                 break;
             }
             pos += 4ll * (1 + w);
-            uint32_t z = 0;
-            for (int k = 0; k < w; ++k) z |= ((p[1 + k] >> lane) & 1u) << k;
+            // lane k + 1 holds plane k: the transpose gives lane i bit k of z_i at bit k + 1
+            const uint32_t z = transpose(lane >= 1 && lane <= w ? q : 0u) >> 1;
             int32_t d = lane ? unzigzag(z) : 0;
 #pragma unroll
             for (int s = 1; s < 32; s <<= 1) {
@@ -305,7 +336,6 @@ __global__ void __launch_bounds__(kThreads) unpack_kernel(const unsigned char *i
                 if (lane >= s) d += y;
             }
             sm[lane * P + x] = (int16_t)((int32_t)(int16_t)(h & 0xffffu) + d);
-            p += 1 + w;
         }
         if (bad) {
             if (lane == 0) atomicOr(err, 2);
