@@ -17,9 +17,10 @@
 // banks), each crystal column's differences are formed with one shuffle, its
 // width with one OR-reduction (the bit length of the OR of the z_i is that of
 // their maximum) and its bit planes with one 32 x 32 bit transpose across the
-// warp, after which the lanes hold the planes in stream order.  A size pass
-// (which also keeps every crystal column's width), an exclusive scan of the
-// block sizes (three kernels) and a write pass that reads the widths back; the
+// warp (shared by two or four columns when their widths allow), after which
+// the lanes hold the planes in stream order.  A size pass (lanes walk crystal
+// columns; it also keeps every column's width), an exclusive scan of the block
+// sizes (three kernels) and a write pass that reads the widths back; the
 // decoder is the same walk backwards (one load of a column's words, the
 // transpose, the differences summed by an inclusive warp scan).  (One ballot
 // per plane, the first form, took 1.5x as long: the integer pipe ran out.  A
@@ -71,31 +72,38 @@ __device__ __forceinline__ int load_block(const int16_t *pool, long long rows, i
     return nv;
 }
 
-// Block sizes, and the width of every crystal column (widths[b][x]).
+// Block sizes, and the width of every crystal column (widths[b][x]).  Lanes
+// take crystal columns here: lane x walks its column down the block's 32 rows
+// (consecutive lanes read consecutive samples of a row: no bank conflict),
+// OR-ing the zigzag differences in a register, so a column costs a few
+// instructions per row shared by 32 columns instead of a shuffle and a
+// reduction of its own.
 __global__ void __launch_bounds__(kThreads) pack_size_kernel(const int16_t *pool, long long rows, int X,
                                                              long long nb, unsigned long long *sizes,
                                                              uint8_t *widths)
 {
     __shared__ __align__(16) int16_t sm_all[kWarps][kBlockElems];
-    __shared__ uint8_t w_all[kWarps][kMaxX];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int16_t *sm = sm_all[warp];
-    uint8_t *wsm = w_all[warp];
-    const int16_t *row = sm + lane * X;
     for (long long b = (long long)blockIdx.x * kWarps + warp; b < nb; b += (long long)gridDim.x * kWarps) {
         load_block(pool, rows, X, b, sm, lane);
         unsigned words = 0;
-        for (int x = 0; x < X; ++x) {
-            const int32_t v = row[x];
-            const uint32_t z = zigzag(v - __shfl_up_sync(kFull, v, 1));  // lane 0: its own value, z = 0
-            const uint32_t m = __reduce_or_sync(kFull, z);
-            const int w = m ? 32 - __clz(m) : 0;
-            wsm[x] = (uint8_t)w;  // every lane: the same byte
+        for (int x = lane; x < X; x += 32) {
+            const int16_t *col = sm + x;
+            int32_t prev = col[0];
+            uint32_t acc = 0;
+#pragma unroll
+            for (int r = 1; r < 32; ++r) {
+                const int32_t v = col[r * X];
+                acc |= zigzag(v - prev);
+                prev = v;
+            }
+            const int w = 32 - __clz(acc);  // 0 for acc = 0
+            widths[b * X + x] = (uint8_t)w;
             words += 1u + (unsigned)w;
         }
+        words = __reduce_add_sync(kFull, words);
         if (lane == 0) sizes[b] = 4ull * words;
-        __syncwarp();
-        for (int x = lane; x < X; x += 32) widths[b * X + x] = wsm[x];
         __syncwarp();
     }
 }
@@ -221,26 +229,33 @@ struct Transpose {
     }
 };
 
-// Crystal columns in pairs (a, b) whenever both widths are <= 16: one
-// transpose of z_a | z_b << 16 puts plane k of a in lane k and plane k of b
-// in lane 16 + k; one store writes both columns' planes, a second the two head
-// words (lane 0 from its own v_a, lane 1 from v_b of row 0, which the
-// difference shuffle brought it).  A column of width 17 (a difference of at
-// least 2^15) goes alone: lane k + 1 of the transposed z << 1 holds plane k,
-// lane 0 the head word.
+// Crystal columns four at a time when all four widths are <= 8 (the common
+// case for noise-dominated island rows), else in pairs (a, b) when both are
+// <= 16, else alone.
+// - Four: one transpose of z_0 | z_1 << 8 | z_2 << 16 | z_3 << 24 puts plane
+//   k of column g in lane 8g + k.  The columns' words lie back to back; byte
+//   g of (w4 + 0x01010101) * 0x01010100 is the words of the columns before g
+//   (w4 = the four widths as bytes).  Lanes 0..3 write the head words, whose
+//   first samples lane 0 broadcasts two to a word.
+// - Two: one transpose of z_a | z_b << 16 puts plane k of a in lane k and of b
+//   in lane 16 + k; lane 0 writes a's head word from its own v_a, lane 1 b's
+//   from v_b of row 0, which the difference shuffle brought it.
+// - Alone (a width of 17: a difference of at least 2^15): lane k + 1 of the
+//   transposed z << 1 holds plane k, lane 0 the head word.
 __global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *pool, long long rows, int X, long long nb,
                                                               const unsigned long long *offs, const uint8_t *widths,
                                                               unsigned char *out, long long cap)
 {
     __shared__ __align__(16) int16_t sm_all[kWarps][kBlockElems];
-    __shared__ uint8_t w_all[kWarps][kMaxX];
+    __shared__ __align__(16) uint8_t w_all[kWarps][kMaxX];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int16_t *sm = sm_all[warp];
     uint8_t *wsm = w_all[warp];
     const int16_t *row = sm + lane * X;
     const Transpose transpose(lane);
-    const int kl = lane & 15;
-    const bool hi = lane >= 16;
+    const int k16 = lane & 15, k8 = lane & 7;
+    const bool hi16 = lane >= 16;
+    const int g8 = 8 * (lane >> 3), h8 = 8 * (lane & 3);  // byte of this lane's group; of its head column
     uint32_t *out32 = reinterpret_cast<uint32_t *>(out);
     const long long head = 16 + 8 * (nb + 1);
     if (blockIdx.x == 0 && threadIdx.x == 0 && cap >= 16) {
@@ -265,20 +280,18 @@ __global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *poo
             if (lane <= w && o + lane < room) dst[o + lane] = word;
             o += 1 + w;
         };
-        int x = 0;
-        for (; x + 1 < X; x += 2) {
+        auto pair = [&](int x) {
             const int wa = wsm[x], wb = wsm[x + 1];
             if (max(wa, wb) > 16) {
                 single(x);
                 single(x + 1);
-                continue;
+                return;
             }
             const int32_t va = row[x], vb = row[x + 1];
             const int32_t pa = __shfl_up_sync(kFull, va, 1), pb = __shfl_up_sync(kFull, vb, 1);
-            const uint32_t za = zigzag(va - pa), zb = zigzag(vb - pb);
-            const uint32_t planes = transpose(za | (zb << 16));
-            const int ip = o + 1 + kl + (hi ? 1 + wa : 0);  // word of this lane's plane
-            if (kl < (hi ? wb : wa) && ip < room) dst[ip] = planes;
+            const uint32_t planes = transpose(zigzag(va - pa) | (zigzag(vb - pb) << 16));
+            const int ip = o + 1 + k16 + (hi16 ? 1 + wa : 0);  // word of this lane's plane
+            if (k16 < (hi16 ? wb : wa) && ip < room) dst[ip] = planes;
             if (lane < 2) {
                 const int ih = lane ? o + 1 + wa : o;
                 const uint32_t hw = lane ? ((uint32_t)(uint16_t)pb | ((uint32_t)wb << 16))
@@ -286,7 +299,35 @@ __global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *poo
                 if (ih < room) dst[ih] = hw;
             }
             o += 2 + wa + wb;
+        };
+        int x = 0;
+        for (; x + 3 < X; x += 4) {
+            const uint32_t w4 = *reinterpret_cast<const uint32_t *>(wsm + x);
+            if ((w4 + 0x77777777u) & 0x80808080u) {  // a width above 8
+                pair(x);
+                pair(x + 2);
+                continue;
+            }
+            const int32_t v0 = row[x], v1 = row[x + 1], v2 = row[x + 2], v3 = row[x + 3];
+            const uint32_t z0 = zigzag(v0 - __shfl_up_sync(kFull, v0, 1));
+            const uint32_t z1 = zigzag(v1 - __shfl_up_sync(kFull, v1, 1));
+            const uint32_t z2 = zigzag(v2 - __shfl_up_sync(kFull, v2, 1));
+            const uint32_t z3 = zigzag(v3 - __shfl_up_sync(kFull, v3, 1));
+            const uint32_t planes = transpose(z0 | (z1 << 8) | (z2 << 16) | (z3 << 24));
+            const uint32_t before = (w4 + 0x01010101u) * 0x01010100u;  // byte g: words of columns < g
+            const int ip = o + (int)((before >> g8) & 0xffu) + 1 + k8;
+            if (k8 < (int)((w4 >> g8) & 0xffu) && ip < room) dst[ip] = planes;
+            const uint32_t h01 = __shfl_sync(kFull, (uint32_t)(uint16_t)v0 | ((uint32_t)v1 << 16), 0);
+            const uint32_t h23 = __shfl_sync(kFull, (uint32_t)(uint16_t)v2 | ((uint32_t)v3 << 16), 0);
+            if (lane < 4) {
+                const uint32_t hp = lane < 2 ? h01 : h23;
+                const uint32_t first = (lane & 1) ? (hp >> 16) : (hp & 0xffffu);
+                const int ih = o + (int)((before >> h8) & 0xffu);
+                if (ih < room) dst[ih] = first | (((w4 >> h8) & 0xffu) << 16);
+            }
+            o += (int)(before >> 24) + 1 + (int)(w4 >> 24);
         }
+        for (; x + 1 < X; x += 2) pair(x);
         if (x < X) single(x);
         __syncwarp();
     }
