@@ -229,19 +229,17 @@ struct Transpose {
     }
 };
 
-// Crystal columns four at a time when all four widths are <= 8 (the common
-// case for noise-dominated island rows), else in pairs (a, b) when both are
-// <= 16, else alone.
-// - Four: one transpose of z_0 | z_1 << 8 | z_2 << 16 | z_3 << 24 puts plane
-//   k of column g in lane 8g + k.  The columns' words lie back to back; byte
-//   g of (w4 + 0x01010101) * 0x01010100 is the words of the columns before g
-//   (w4 = the four widths as bytes).  Lanes 0..3 write the head words, whose
-//   first samples lane 0 broadcasts two to a word.
-// - Two: one transpose of z_a | z_b << 16 puts plane k of a in lane k and of b
-//   in lane 16 + k; lane 0 writes a's head word from its own v_a, lane 1 b's
-//   from v_b of row 0, which the difference shuffle brought it.
-// - Alone (a width of 17: a difference of at least 2^15): lane k + 1 of the
-//   transposed z << 1 holds plane k, lane 0 the head word.
+// Crystal columns go through the transpose four at a time when all four
+// widths are <= 7 (the common case for noise-dominated island rows), else in
+// pairs when both are <= 15, else alone.  A group of G = 8, 16 or 32 lanes
+// serves one column: its z << 1 sits at bit G g of the transposed word, so
+// lane G g + k + 1 receives plane k and the group's first lane, which receives
+// zeros, carries the head word instead.  One store then writes every column's
+// words, which lie back to back: the head, then the planes.
+// - Four: byte g of (w4 + 0x01010101) * 0x01010100 is the words of the columns
+//   before g (w4 = the four widths as bytes); lane 0 broadcasts the first
+//   samples two to a word.
+// - Alone (a width of 16 or 17: a difference of at least 2^14).
 __global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *pool, long long rows, int X, long long nb,
                                                               const unsigned long long *offs, const uint8_t *widths,
                                                               unsigned char *out, long long cap)
@@ -255,7 +253,7 @@ __global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *poo
     const Transpose transpose(lane);
     const int k16 = lane & 15, k8 = lane & 7;
     const bool hi16 = lane >= 16;
-    const int g8 = 8 * (lane >> 3), h8 = 8 * (lane & 3);  // byte of this lane's group; of its head column
+    const int g4 = lane >> 3, g8 = 8 * g4;  // four-column group of this lane, its byte
     uint32_t *out32 = reinterpret_cast<uint32_t *>(out);
     const long long head = 16 + 8 * (nb + 1);
     if (blockIdx.x == 0 && threadIdx.x == 0 && cap >= 16) {
@@ -282,28 +280,26 @@ __global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *poo
         };
         auto pair = [&](int x) {
             const int wa = wsm[x], wb = wsm[x + 1];
-            if (max(wa, wb) > 16) {
+            if (max(wa, wb) > 15) {
                 single(x);
                 single(x + 1);
                 return;
             }
             const int32_t va = row[x], vb = row[x + 1];
-            const int32_t pa = __shfl_up_sync(kFull, va, 1), pb = __shfl_up_sync(kFull, vb, 1);
-            const uint32_t planes = transpose(zigzag(va - pa) | (zigzag(vb - pb) << 16));
-            const int ip = o + 1 + k16 + (hi16 ? 1 + wa : 0);  // word of this lane's plane
-            if (k16 < (hi16 ? wb : wa) && ip < room) dst[ip] = planes;
-            if (lane < 2) {
-                const int ih = lane ? o + 1 + wa : o;
-                const uint32_t hw = lane ? ((uint32_t)(uint16_t)pb | ((uint32_t)wb << 16))
-                                         : ((uint32_t)(uint16_t)va | ((uint32_t)wa << 16));
-                if (ih < room) dst[ih] = hw;
-            }
+            const uint32_t za = zigzag(va - __shfl_up_sync(kFull, va, 1));
+            const uint32_t zb = zigzag(vb - __shfl_up_sync(kFull, vb, 1));
+            const uint32_t planes = transpose((za << 1) | (zb << 17));
+            const uint32_t firsts = __shfl_sync(kFull, (uint32_t)(uint16_t)va | ((uint32_t)vb << 16), 0);
+            const int w = hi16 ? wb : wa;
+            const uint32_t hw = (hi16 ? firsts >> 16 : firsts & 0xffffu) | ((uint32_t)w << 16);
+            const int i = o + (hi16 ? 1 + wa : 0) + k16;
+            if (k16 <= w && i < room) dst[i] = k16 ? planes : hw;
             o += 2 + wa + wb;
         };
         int x = 0;
         for (; x + 3 < X; x += 4) {
             const uint32_t w4 = *reinterpret_cast<const uint32_t *>(wsm + x);
-            if ((w4 + 0x77777777u) & 0x80808080u) {  // a width above 8
+            if ((w4 + 0x78787878u) & 0x80808080u) {  // a width above 7
                 pair(x);
                 pair(x + 2);
                 continue;
@@ -313,18 +309,15 @@ __global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *poo
             const uint32_t z1 = zigzag(v1 - __shfl_up_sync(kFull, v1, 1));
             const uint32_t z2 = zigzag(v2 - __shfl_up_sync(kFull, v2, 1));
             const uint32_t z3 = zigzag(v3 - __shfl_up_sync(kFull, v3, 1));
-            const uint32_t planes = transpose(z0 | (z1 << 8) | (z2 << 16) | (z3 << 24));
+            const uint32_t planes = transpose((z0 << 1) | (z1 << 9) | (z2 << 17) | (z3 << 25));
+            const uint32_t f01 = __shfl_sync(kFull, (uint32_t)(uint16_t)v0 | ((uint32_t)v1 << 16), 0);
+            const uint32_t f23 = __shfl_sync(kFull, (uint32_t)(uint16_t)v2 | ((uint32_t)v3 << 16), 0);
+            const uint32_t fp = g4 < 2 ? f01 : f23;
+            const uint32_t w = (w4 >> g8) & 0xffu;
+            const uint32_t hw = ((g4 & 1) ? fp >> 16 : fp & 0xffffu) | (w << 16);
             const uint32_t before = (w4 + 0x01010101u) * 0x01010100u;  // byte g: words of columns < g
-            const int ip = o + (int)((before >> g8) & 0xffu) + 1 + k8;
-            if (k8 < (int)((w4 >> g8) & 0xffu) && ip < room) dst[ip] = planes;
-            const uint32_t h01 = __shfl_sync(kFull, (uint32_t)(uint16_t)v0 | ((uint32_t)v1 << 16), 0);
-            const uint32_t h23 = __shfl_sync(kFull, (uint32_t)(uint16_t)v2 | ((uint32_t)v3 << 16), 0);
-            if (lane < 4) {
-                const uint32_t hp = lane < 2 ? h01 : h23;
-                const uint32_t first = (lane & 1) ? (hp >> 16) : (hp & 0xffffu);
-                const int ih = o + (int)((before >> h8) & 0xffu);
-                if (ih < room) dst[ih] = first | (((w4 >> h8) & 0xffu) << 16);
-            }
+            const int i = o + (int)((before >> g8) & 0xffu) + k8;
+            if (k8 <= (int)w && i < room) dst[i] = k8 ? planes : hw;
             o += (int)(before >> 24) + 1 + (int)(w4 >> 24);
         }
         for (; x + 1 < X; x += 2) pair(x);
