@@ -737,7 +737,24 @@ def bench_pack(args, torch, dev, daq, pool, rows: int) -> dict:
     raw = rows * X * 2
     alg = 2 * raw + n        # the pool is read by the size pass and by the write pass
     peak = measured_peaks()[0]
-    del out, ws
+    # decoding the stream back into pool rows (checked against the pool once)
+    back = torch.empty((rows, X), dtype=torch.int16, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def decode():
+        rc = daq.daq_unpack_pool(out.data_ptr(), n, rows, X, back.data_ptr(), err.data_ptr(), stream.cuda_stream)
+        assert rc == daq.DAQ_OK, rc
+
+    decode()
+    torch.cuda.synchronize(dev)
+    assert int(err.item()) == 0 and torch.equal(back, pool[:rows]), "decoded pool differs"
+    e0.record(stream)
+    for _ in range(K):
+        decode()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ums = e0.elapsed_time(e1) / K
+    del out, ws, back
     torch.cuda.empty_cache()
     return {"value": round(raw / (ms * 1e-3) / 1e9, 2), "unit": "GB/s of pool rows packed", "steps": K,
             "ms_per_fill": round(ms, 4), "pool_bytes": raw, "packed_bytes": n,
@@ -745,6 +762,8 @@ def bench_pack(args, torch, dev, daq, pool, rows: int) -> dict:
             "workload": "pool rows of the full fill (24 x 54 x 560,000, T=30, pre=8, post=24)",
             "roofline": {"bound": "hbm", "achieved": round(alg / (ms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4), "algorithmic_bytes_per_launch": alg},
+            "unpack": {"value": round(raw / (ums * 1e-3) / 1e9, 2), "unit": "GB/s of pool rows decoded",
+                       "ms_per_fill": round(ums, 4), "steps": K, "gpu_launches": K},
             "gpu_launches": 5 * K}
 
 

@@ -350,26 +350,66 @@ __global__ void __launch_bounds__(kThreads) unpack_kernel(const unsigned char *i
         const unsigned long long off = offs[b];
         bool bad = off > (unsigned long long)(in_bytes - head) || (off & 3ull);
         long long pos = head + (long long)(bad ? 0ull : off);  // bytes read so far end at pos
-        for (int x = 0; x < X && !bad; ++x) {
-            // the column's head word and planes: one load of up to 18 words
+        for (int x = 0; x < X && !bad;) {
+            // the next 32 words: up to four columns' head words and planes
             const uint32_t *p = reinterpret_cast<const uint32_t *>(in + pos);
-            const uint32_t q = lane < 18 && pos + 4ll * lane + 4 <= in_bytes ? p[lane] : 0u;
-            const uint32_t h = __shfl_sync(kFull, q, 0);
-            const int w = (int)(h >> 16);
-            if (pos + 4 > in_bytes || w > 17 || pos + 4ll * (1 + w) > in_bytes) {
+            const uint32_t q = pos + 4ll * lane + 4 <= in_bytes ? p[lane] : 0u;
+            const uint32_t h0 = __shfl_sync(kFull, q, 0);
+            const int w0 = (int)(h0 >> 16);
+            // four columns of width <= 7 at once: their head words lie at 0, i1, i2, i3
+            const int i1 = 1 + min(w0, 8);
+            const uint32_t h1 = __shfl_sync(kFull, q, i1);
+            const int w1 = (int)(h1 >> 16), i2 = i1 + 1 + min(w1, 8);
+            const uint32_t h2 = __shfl_sync(kFull, q, i2);
+            const int w2 = (int)(h2 >> 16), i3 = i2 + 1 + min(w2, 8);
+            const uint32_t h3 = __shfl_sync(kFull, q, i3);
+            const int w3 = (int)(h3 >> 16), total = i3 + 1 + min(w3, 8);
+            if (x + 3 < X && max(max(w0, w1), max(w2, w3)) <= 7 && pos + 4ll * total <= in_bytes) {
+                // lane 8g + k + 1 takes plane k of column g: the transpose gives lane i
+                // bit k of z_{g,i} at bit 8g + k + 1
+                const int g = lane >> 3, k = lane & 7;
+                const int ig = g == 0 ? 0 : g == 1 ? i1 : g == 2 ? i2 : i3;
+                const int wg = g == 0 ? w0 : g == 1 ? w1 : g == 2 ? w2 : w3;
+                const uint32_t pl = __shfl_sync(kFull, q, (ig + k) & 31);
+                const uint32_t t = transpose(k >= 1 && k <= wg ? pl : 0u);
+                // |difference| <= 64, so 32 of them sum below 2^15: two columns share a scan
+                int32_t d01 = lane ? unzigzag((t >> 1) & 0x7fu) + unzigzag((t >> 9) & 0x7fu) * 65536 : 0;
+                int32_t d23 = lane ? unzigzag((t >> 17) & 0x7fu) + unzigzag((t >> 25) & 0x7fu) * 65536 : 0;
+#pragma unroll
+                for (int s = 1; s < 32; s <<= 1) {
+                    const int32_t y01 = __shfl_up_sync(kFull, d01, s), y23 = __shfl_up_sync(kFull, d23, s);
+                    if (lane >= s) {
+                        d01 += y01;
+                        d23 += y23;
+                    }
+                }
+                const int32_t s0 = (int16_t)(d01 & 0xffff), s2 = (int16_t)(d23 & 0xffff);
+                const int32_t s1 = (d01 - s0) >> 16, s3 = (d23 - s2) >> 16;
+                int16_t *r = sm + lane * P + x;
+                r[0] = (int16_t)((int32_t)(int16_t)(h0 & 0xffffu) + s0);
+                r[1] = (int16_t)((int32_t)(int16_t)(h1 & 0xffffu) + s1);
+                r[2] = (int16_t)((int32_t)(int16_t)(h2 & 0xffffu) + s2);
+                r[3] = (int16_t)((int32_t)(int16_t)(h3 & 0xffffu) + s3);
+                pos += 4ll * total;
+                x += 4;
+                continue;
+            }
+            // one column
+            if (pos + 4 > in_bytes || w0 > 17 || pos + 4ll * (1 + w0) > in_bytes) {
                 bad = true;
                 break;
             }
-            pos += 4ll * (1 + w);
+            pos += 4ll * (1 + w0);
             // lane k + 1 holds plane k: the transpose gives lane i bit k of z_i at bit k + 1
-            const uint32_t z = transpose(lane >= 1 && lane <= w ? q : 0u) >> 1;
+            const uint32_t z = transpose(lane >= 1 && lane <= w0 ? q : 0u) >> 1;
             int32_t d = lane ? unzigzag(z) : 0;
 #pragma unroll
             for (int s = 1; s < 32; s <<= 1) {
                 const int32_t y = __shfl_up_sync(kFull, d, s);
                 if (lane >= s) d += y;
             }
-            sm[lane * P + x] = (int16_t)((int32_t)(int16_t)(h & 0xffffu) + d);
+            sm[lane * P + x] = (int16_t)((int32_t)(int16_t)(h0 & 0xffffu) + d);
+            ++x;
         }
         if (bad) {
             if (lane == 0) atomicOr(err, 2);
