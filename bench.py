@@ -328,17 +328,23 @@ def bench_gb300(args, ws, rank, local):
         for _ in range(2):
             rc = daq.daq_process_fills_host(C, X, N, F, pe, isl, q.data_ptr(), io)
             assert rc == daq.DAQ_OK, rc
+        # the link's rates just before the timed calls (others' traffic on a shared host lowers them)
+        bw_before = copy_bandwidth(torch, dev, host, samples, pool_h, out.pool, int(counts_h[1]))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
+        call_ms = []
         e0.record(stream)
         for _ in range(Ke):
+            tc = time.perf_counter()
             daq.daq_process_fills_host(C, X, N, F, pe, isl, q.data_ptr(), io)
+            call_ms.append((time.perf_counter() - tc) * 1e3)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ems = e0.elapsed_time(e1)
         _, ems, e2e_value = replicas.aggregate(Ke * raw_bytes, ems, dev)
         d2h = 32 + int(counts_h[0]) * 24 + int(counts_h[1]) * X * 2
         bw = copy_bandwidth(torch, dev, host, samples, pool_h, out.pool, int(counts_h[1]))
+        bw["before_e2e"] = {k: bw_before[k] for k in ("h2d_gbs", "d2h_gbs", "bidir_gbs", "median")}
         e2e_bound = raw_bytes / max(raw_bytes / bw["h2d_gbs"], d2h / bw["d2h_gbs"],
                                     (raw_bytes + d2h) / bw["bidir_gbs"]) if bw["h2d_gbs"] else None
         # the same through the packed host form (pool rows leave the GPU packed)
@@ -366,6 +372,8 @@ def bench_gb300(args, ws, rank, local):
         result["e2e"] = {"value": round(e2e_value, 2), "unit": UNIT,
                          "h2d_bytes_per_step": raw_bytes, "d2h_bytes_per_step": d2h, "steps": Ke,
                          "ms_per_step": round(ems / Ke, 3),
+                         "call_ms": {"min": round(min(call_ms), 3), "p50": round(statistics.median(call_ms), 3),
+                                     "max": round(max(call_ms), 3)},
                          "api": "daq_process_fills_host (pinned host buffers; copy-in, processing and copy-out "
                                 "pipelined over calorimeter chunks)",
                          "copy_bandwidth": bw,
@@ -514,7 +522,7 @@ def copy_bandwidth(torch, dev, host_in, dev_in, host_out, dev_out, out_rows: int
     def timed(fn):
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        best = None
+        times = []
         for _ in range(reps):
             e0.record(torch.cuda.current_stream(dev))
             fn()
@@ -522,9 +530,8 @@ def copy_bandwidth(torch, dev, host_in, dev_in, host_out, dev_out, out_rows: int
                 torch.cuda.current_stream(dev).wait_stream(st)
             e1.record(torch.cuda.current_stream(dev))
             torch.cuda.synchronize(dev)
-            ms = e0.elapsed_time(e1)
-            best = ms if best is None else min(best, ms)
-        return best
+            times.append(e0.elapsed_time(e1))
+        return min(times), statistics.median(times)
 
     def h2d():
         a.wait_stream(torch.cuda.current_stream(dev))
@@ -540,11 +547,13 @@ def copy_bandwidth(torch, dev, host_in, dev_in, host_out, dev_out, out_rows: int
         h2d()
         d2h()
 
-    t_in, t_out, t_both = timed(h2d), timed(d2h), timed(both)
-    return {"h2d_gbs": round(nb_in / (t_in * 1e-3) / 1e9, 1), "d2h_gbs": round(nb_out / (t_out * 1e-3) / 1e9, 1),
-            "bidir_gbs": round((nb_in + nb_out) / (t_both * 1e-3) / 1e9, 1),
-            "method": "best of 3 pinned cudaMemcpyAsync of the fill (h2d) and of its pool rows (d2h), "
-                      "alone and concurrently on two streams"}
+    (t_in, m_in), (t_out, m_out), (t_both, m_both) = timed(h2d), timed(d2h), timed(both)
+    gbs = lambda nb, ms: round(nb / (ms * 1e-3) / 1e9, 1)
+    return {"h2d_gbs": gbs(nb_in, t_in), "d2h_gbs": gbs(nb_out, t_out), "bidir_gbs": gbs(nb_in + nb_out, t_both),
+            "median": {"h2d_gbs": gbs(nb_in, m_in), "d2h_gbs": gbs(nb_out, m_out),
+                       "bidir_gbs": gbs(nb_in + nb_out, m_both)},
+            "method": f"best (and median) of {reps} pinned cudaMemcpyAsync of the fill (h2d) and of its pool rows "
+                      "(d2h), alone and concurrently on two streams"}
 
 
 def time_calls(torch, dev, daq, x, F, C, X, N, params, K: int, out=None, warm: int = 2):
