@@ -23,6 +23,7 @@ def test_bounds_and_argument_checks(daq):
     assert daq.daq_pack_workspace_size(1000, 54) > 0
     assert daq.daq_pack_pool(0, 0, 65, 0, 0, 8, 0, 0, None) == daq.DAQ_EUNSUPPORTED     # n_xtal > 64
     assert daq.daq_pack_pool(0, 10, 4, 0, 0, None, 0, 0, None) == daq.DAQ_EINVAL      # no out_bytes
+    assert daq.daq_pack_pool(2, 10, 4, 16, 1000, 8, 16, 4096, None) == daq.DAQ_EINVAL  # pool not 16-byte aligned
     assert daq.daq_unpack_pool(None, 100, 10, 4, 0, 0, None) == daq.DAQ_EINVAL
 
 
