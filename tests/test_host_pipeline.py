@@ -40,7 +40,10 @@ def split_streams(buf: np.ndarray, total: int) -> list:
     return out
 
 
-def run_host(env, s, params, fill_len=None, dev_rows=None, dev_hdr=None, host_rows=None, q=None, pack=False):
+def run_host(env, s, params, fill_len=None, dev_rows=None, dev_hdr=None, host_rows=None, q=None, pack=False,
+             locked_out=True):
+    """locked_out: page-locked record and pool buffers (the device writes them);
+    else pageable ones (copy engines after host waits)."""
     torch, daq = env["torch"], env["daq"]
     F, C, X, N = s.shape
     host = torch.from_numpy(s).pin_memory()
@@ -49,8 +52,14 @@ def run_host(env, s, params, fill_len=None, dev_rows=None, dev_hdr=None, host_ro
     out = daq.Outputs(torch, "cuda", F, C, X, dev_hdr if dev_hdr is not None else F * C * ((N + 1) // 2),
                       dev_rows if dev_rows is not None else rows)
     hrows = host_rows if host_rows is not None else F * C * N
-    hdr_h = np.zeros(max(1, F * C * N // 2 + F * C), daq.ISLAND_DTYPE)
-    pool_h = torch.empty((max(1, hrows), X), dtype=torch.int16).pin_memory()
+    n_rec = max(1, F * C * N // 2 + F * C)
+    if locked_out:
+        hdr_t = torch.zeros(n_rec * daq.ISLAND_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+        hdr_h = hdr_t.numpy().view(daq.ISLAND_DTYPE)
+        pool_t = torch.zeros((max(1, hrows), X), dtype=torch.int16).pin_memory()
+    else:
+        hdr_t, hdr_h = None, np.zeros(n_rec, daq.ISLAND_DTYPE)
+        pool_t = torch.from_numpy(np.zeros((max(1, hrows), X), np.int16))
     ped_h = np.zeros((F, C, X), np.int32)
     counts_h = np.zeros(4, np.int64)
     if q is None:
@@ -60,7 +69,7 @@ def run_host(env, s, params, fill_len=None, dev_rows=None, dev_hdr=None, host_ro
     p = daq.make_params(**params, fill_len=fl, stream=stream)
     ws = torch.empty(daq.daq_workspace_size(C, X, N, F, p), dtype=torch.uint8, device="cuda")
     p.workspace, p.workspace_bytes = ws.data_ptr(), ws.numel()
-    io = daq.DaqHostIO(host.data_ptr(), sdev.data_ptr(), hdr_h.ctypes.data, len(hdr_h), pool_h.data_ptr(), hrows,
+    io = daq.DaqHostIO(host.data_ptr(), sdev.data_ptr(), hdr_h.ctypes.data, len(hdr_h), pool_t.data_ptr(), hrows,
                        ped_h.ctypes.data, counts_h.ctypes.data)
     if pack:
         p.flags |= daq.DAQ_PACK_POOL
@@ -74,8 +83,8 @@ def run_host(env, s, params, fill_len=None, dev_rows=None, dev_hdr=None, host_ro
     if pack:
         pool = [env["oracle"].unpack(st, rows, xx) for st, rows, xx in split_streams(phost, int(pbytes[0]))]
         pool = np.concatenate(pool) if pool else np.zeros((0, X), np.int16)
-        return rc, counts_h, hdr_h, pool, ped_h, q
-    return rc, counts_h, hdr_h, pool_h.numpy(), ped_h, q
+        return rc, counts_h, hdr_h.copy(), pool, ped_h, q
+    return rc, counts_h, hdr_h.copy(), pool_t.numpy().copy(), ped_h, q
 
 
 def check(res, ref):
@@ -89,13 +98,15 @@ def check(res, ref):
     assert np.array_equal(q.cpu().numpy(), ref["q"])
 
 
-@pytest.mark.parametrize("F,C,N", [(1, 24, 20_000), (1, 5, 33_000), (3, 2, 16_000), (16, 3, 8_000), (1, 1, 50_000)])
-def test_pipelined_host_form_matches_oracle(env, F, C, N):
+@pytest.mark.parametrize("locked_out", [True, False])
+@pytest.mark.parametrize("F,C,N", [(1, 24, 20_000), (1, 5, 33_000), (3, 2, 16_000), (16, 3, 8_000), (1, 1, 50_000),
+                                   (2, 3, 20_001)])
+def test_pipelined_host_form_matches_oracle(env, F, C, N, locked_out):
     from synth import workloads as W
     w = W.scaled(W.PLAIN_FULL_FILL, n_fills=F, n_calo=C, n_samples=N)
     s = env["synth"].generate(w.config())
     ref = env["oracle"].process_fills(s, w.params(), n_threads=8)
-    check(run_host(env, s, w.params()), ref)
+    check(run_host(env, s, w.params(), locked_out=locked_out), ref)
 
 
 def test_host_form_with_fill_lengths_and_two_decimations(env):
@@ -107,21 +118,23 @@ def test_host_form_with_fill_lengths_and_two_decimations(env):
     check(run_host(env, s, w.params(), fill_len=fl), ref)
 
 
-def test_host_form_single_chunk_when_device_capacity_is_small(env):
+@pytest.mark.parametrize("locked_out", [True, False])
+def test_host_form_single_chunk_when_device_capacity_is_small(env, locked_out):
     from synth import workloads as W
     w = W.scaled(W.PLAIN_FULL_FILL, n_calo=6, n_samples=20_000)
     s = env["synth"].generate(w.config())
     ref = env["oracle"].process_fills(s, w.params(), n_threads=8)
     rows = ref["n_rows"] + 1000                     # enough for the result, not for every chunk's worst case
-    check(run_host(env, s, w.params(), dev_rows=rows, dev_hdr=ref["n_islands"] + 10), ref)
+    check(run_host(env, s, w.params(), dev_rows=rows, dev_hdr=ref["n_islands"] + 10, locked_out=locked_out), ref)
 
 
-def test_host_form_reports_short_host_capacity(env):
+@pytest.mark.parametrize("locked_out", [True, False])
+def test_host_form_reports_short_host_capacity(env, locked_out):
     from synth import workloads as W
     w = W.scaled(W.PLAIN_FULL_FILL, n_calo=4, n_samples=20_000)
     s = env["synth"].generate(w.config())
     ref = env["oracle"].process_fills(s, w.params(), n_threads=8)
-    rc, counts, hdr, pool, ped, q = run_host(env, s, w.params(), host_rows=ref["n_rows"] // 2)
+    rc, counts, hdr, pool, ped, q = run_host(env, s, w.params(), host_rows=ref["n_rows"] // 2, locked_out=locked_out)
     assert rc == env["daq"].DAQ_ECAPACITY
     assert int(counts[1]) == ref["n_rows"] and int(counts[0]) == ref["n_islands"]
     assert np.array_equal(pool[: ref["n_rows"] // 2], ref["pool"][: ref["n_rows"] // 2])
