@@ -373,7 +373,7 @@ def bench_gb300(args, ws, rank, local):
                          "h2d_bytes_per_step": raw_bytes, "d2h_bytes_per_step": d2h, "steps": Ke,
                          "ms_per_step": round(ems / Ke, 3),
                          "call_ms": {"min": round(min(call_ms), 3), "p50": round(statistics.median(call_ms), 3),
-                                     "max": round(max(call_ms), 3)},
+                                     "max": round(max(call_ms), 3), "all": [round(t, 2) for t in call_ms]},
                          "api": "daq_process_fills_host (pinned host buffers; copy-in, processing and copy-out "
                                 "pipelined over calorimeter chunks)",
                          "copy_bandwidth": bw,

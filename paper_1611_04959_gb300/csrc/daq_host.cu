@@ -22,7 +22,8 @@
 namespace {
 
 constexpr int kMaxChunks = 64;
-constexpr int kTargetChunks = 8;
+constexpr int kTargetChunks = 8;         // rows copied back as they are
+constexpr int kTargetChunksPacked = 24;  // rows packed on the GPU first
 constexpr int kMaxDevices = 64;
 
 // Streams, events and count buffers of the pipeline, created on a device's
@@ -78,14 +79,14 @@ struct Chunk {
     int64_t pk_off, pk_cap;                      // device region of the packed stream
 };
 
-// Chunks of about U / kTargetChunks calorimeter-fills, never splitting a
+// Chunks of about U / target calorimeter-fills, never splitting a
 // calorimeter-fill and never mixing parts of two fills.
-std::vector<Chunk> make_chunks(int F, int C)
+std::vector<Chunk> make_chunks(int F, int C, int target)
 {
     std::vector<Chunk> v;
     const int64_t U = (int64_t)F * C;
     if (U == 0) return v;
-    const int64_t u = (U + kTargetChunks - 1) / kTargetChunks;
+    const int64_t u = (U + target - 1) / target;
     if (u >= C) {
         const int m = (int)(u / C);
         for (int f = 0; f < F; f += m) v.push_back(Chunk{f, std::min(m, F - f), 0, C, 0, 0, 0, 0, 0, 0, 0, 0, 0});
@@ -133,7 +134,7 @@ extern "C" int daq_process_fills_host(int n_calo, int n_xtal, int64_t n_samples,
     // Chunk plan; each chunk's device region holds its worst case (every
     // sample marked; an island per two samples), rows rounded to 8 so every
     // region starts 16-byte aligned.  Too little device capacity: one chunk.
-    std::vector<Chunk> ch = make_chunks(n_fills, n_calo);
+    std::vector<Chunk> ch = make_chunks(n_fills, n_calo, pack ? kTargetChunksPacked : kTargetChunks);
     if (ch.empty()) ch.push_back(Chunk{0, n_fills, 0, n_calo, 0, 0, 0, 0, 0, 0, 0, 0, 0});
     {
         int64_t h = 0, r = 0;
