@@ -636,6 +636,16 @@ def bench_sparse(args, torch, dev, daq, synth, W) -> dict:
             "kernels_ms": kern, "gpu_launches": 4 * K}
 
 
+def plan_tile(daq, F, C, X, N, params) -> int | None:
+    """The tile width the default plan takes for these sizes and windows (read
+    back through its tile count)."""
+    tiles = daq.daq_trace_tiles(C, X, N, F, daq.make_params(**params))
+    for tw in (448, 384, 224, 128):
+        if tiles == F * C * -(-N // tw):
+            return tw
+    return None
+
+
 def bench_stress(args, torch, dev, daq, synth, W) -> dict:
     """The stress workload: 48 fills x 24 calorimeters x 54 x 560,000 int16
     (69.67 GB device-resident), 10x pulse rate, T=15, post=64, D in {8, 32},
@@ -674,7 +684,7 @@ def bench_stress(args, torch, dev, daq, synth, W) -> dict:
            "raw_bytes_per_batch": raw, "islands_per_batch": int(counts[0]), "pool_rows_per_batch": int(counts[1]),
            "coverage": round(int(counts[1]) / (F * C * N), 6), "status": status,
            "output_sizes": "computed on the device (counts) in the same call", "gpu_launches": 4 * Ks,
-           "kernels_ms": kern,
+           "kernels_ms": kern, "tile": plan_tile(daq, F, C, X, N, params),
            "generation_s": round(gen_s, 1)}
     del x, out
     torch.cuda.empty_cache()

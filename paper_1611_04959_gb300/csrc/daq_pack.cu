@@ -12,21 +12,22 @@
 // row differences of a crystal are small (noise, pulse edges) and a block's
 // crystal column typically needs a few bits per sample instead of 16.
 //
-// One warp per block: the block's rows are copied to shared memory (row pitch
-// an odd number of words, so a warp reading one crystal down 32 rows hits 32
-// banks), each crystal column's differences are formed with one shuffle, its
-// width with one OR-reduction (the bit length of the OR of the z_i is that of
-// their maximum) and its bit planes with one 32 x 32 bit transpose across the
-// warp (shared by two or four columns when their widths allow), after which
-// the lanes hold the planes in stream order.  A size pass (lanes walk crystal
-// columns; it also keeps every column's width), an exclusive scan of the block
-// sizes (three kernels) and a write pass that reads the widths back; the
-// decoder is the same walk backwards (one load of a column's words, the
-// transpose, the differences summed by an inclusive warp scan).  (One ballot
-// per plane, the first form, took 1.5x as long: the integer pipe ran out.  A
-// single pass whose warps found their block's place by decoupled look-back was
-// 2.3x slower: with thousands of one-block warps in flight the nearest
-// published prefix lies hundreds of blocks back.)
+// One warp per block; the block's rows are copied to shared memory as 16-byte
+// vectors.  The size pass puts lanes on crystal columns: a lane walks its
+// column down the 32 rows OR-ing the zigzag differences (the bit length of the
+// OR is that of the maximum: the column's width) and the block's size
+// follows.  An exclusive scan of the block sizes (three kernels) gives the
+// offsets.  The write pass puts lanes on rows (row pitch an odd number of
+// words, so a warp reading one crystal down 32 rows hits 32 banks): one
+// shuffle forms a column's differences and one 32 x 32 bit transpose across
+// the warp turns them into bit planes held by lanes in stream order, shared
+// by two or four columns when their widths allow.  The decoder is the same
+// walk backwards (one load of the columns' words, the transpose, the
+// differences summed by an inclusive warp scan).  (One ballot per plane, the
+// first form, took 2.7x as long: the integer pipe ran out.  A single pass
+// whose warps found their block's place by decoupled look-back was slower
+// still: with thousands of one-block warps in flight the nearest published
+// prefix lies hundreds of blocks back.)
 #include <cuda_runtime.h>
 
 #include <algorithm>
