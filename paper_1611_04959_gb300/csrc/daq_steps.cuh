@@ -301,17 +301,22 @@ __device__ __forceinline__ void sum_pass_step(const KArgs &a, const TileInfo &T,
     uint32_t *row1 = row0 + (a.srow >> 2);
     int acc0 = 0, acc1 = 0;
     if (have) {
+        // even and odd crystals in separate accumulators: two dependency chains
+        // of X/2 dp2a each instead of one of X
+        int acc0b = 0, acc1b = 0;
 #pragma unroll 9
         for (int x = 0; x < X; x += 2) {
             const uint32_t w0 = lds_u32(base + (uint32_t)(x * a.rs));
             const uint32_t w1 = x + 1 < X ? lds_u32(base + (uint32_t)((x + 1) * a.rs)) : 0u;
             acc0 = __dp2a_lo((int)w0, 0x0001, acc0);
             acc1 = __dp2a_lo((int)w0, 0x0100, acc1);
-            acc0 = __dp2a_lo((int)w1, 0x0001, acc0);
-            acc1 = __dp2a_lo((int)w1, 0x0100, acc1);
+            acc0b = __dp2a_lo((int)w1, 0x0001, acc0b);
+            acc1b = __dp2a_lo((int)w1, 0x0100, acc1b);
             if (st0) row0[x >> 1] = __byte_perm(w0, w1, 0x5410);
             if (st1) row1[x >> 1] = __byte_perm(w0, w1, 0x7632);
         }
+        acc0 += acc0b;
+        acc1 += acc1b;
     }
     const int S0 = acc0 - T.ptot, S1 = acc1 - T.ptot;
     const bool in0 = have && t >= 0 && t < T.len, in1 = have && t + 1 >= 0 && t + 1 < T.len;
