@@ -21,6 +21,7 @@ import glob
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -49,9 +50,14 @@ KERNEL_SOURCES = ("daq_device.cuh", "daq_steps.cuh", "daq_twopass.cuh", "daq_pro
 
 
 def kernel_source_hash() -> str:
+    """Hash of the code (comments and whitespace left out, so that editing a
+    comment does not void a profile taken on the same kernels)."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_1611_04959_gb300", "csrc", name), "rb").read())
+        text = open(os.path.join(ROOT, "paper_1611_04959_gb300", "csrc", name), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

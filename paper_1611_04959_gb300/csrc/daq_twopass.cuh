@@ -6,9 +6,11 @@
 //                       the tile), Q-method partial bins; stores the tile's marks
 //                       words and its aggregate (marked samples, island starts,
 //                       trailing run).  No tile waits on another.
-//   daq_scan_*_kernels  reduce-then-scan of the per-tile aggregates: every tile's
-//                       exclusive prefix (pool row and island index it starts
-//                       at, marked run entering it) and the call's totals.
+//   daq_scan_kernel     chained scan of the per-tile aggregates (blocks ordered
+//                       by a ticket, decoupled look-back over earlier blocks):
+//                       every tile's exclusive prefix (pool row and island
+//                       index it starts at, marked run entering it) and the
+//                       call's totals.
 //   daq_compact_kernel  every tile again (tile proper only): the raw samples of
 //                       its marked times are transposed into rows in shared
 //                       memory at the phase of their global position, written
