@@ -22,7 +22,7 @@
 namespace {
 
 constexpr int kMaxChunks = 64;
-constexpr int kTargetChunks = 8;         // rows copied back as they are
+constexpr int kTargetChunks = 12;        // rows copied back as they are
 constexpr int kTargetChunksPacked = 24;  // rows packed on the GPU first
 constexpr int kMaxDevices = 64;
 
