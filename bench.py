@@ -367,9 +367,12 @@ def bench_gb300(args, ws, rank, local):
             rc = daq.daq_process_fills_host(C, X, N, F, pp_, isl, q.data_ptr(), io)
             assert rc == daq.DAQ_OK, rc
         barrier()
+        pk_call_ms = []
         e0.record(stream)
         for _ in range(Ke):
+            tc = time.perf_counter()
             daq.daq_process_fills_host(C, X, N, F, pp_, isl, q.data_ptr(), io)
+            pk_call_ms.append((time.perf_counter() - tc) * 1e3)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         _, pms, pk_value = replicas.aggregate(Ke * raw_bytes, e0.elapsed_time(e1), dev)
@@ -385,6 +388,10 @@ def bench_gb300(args, ws, rank, local):
                          "copy_bandwidth": bw,
                          "bound_gbs": None if e2e_bound is None else round(e2e_bound, 2),
                          "packed": {"value": round(pk_value, 2), "unit": UNIT, "ms_per_step": round(pms / Ke, 3),
+                                    "call_ms": {"min": round(min(pk_call_ms), 3),
+                                                "p50": round(statistics.median(pk_call_ms), 3),
+                                                "max": round(max(pk_call_ms), 3),
+                                                "all": [round(t, 2) for t in pk_call_ms]},
                                     "h2d_bytes_per_step": raw_bytes, "d2h_bytes_per_step": pk_d2h,
                                     "api": "daq_process_fills_host with DAQ_PACK_POOL (pool rows packed losslessly "
                                            "on the GPU before the copy back)"}}
