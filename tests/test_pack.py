@@ -64,6 +64,24 @@ def test_stream_matches_oracle_and_round_trips(env, rows, X):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("rows,X", [(777, 54), (4096 + 13, 7), (2000, 64), (1500, 9)])
+def test_every_width_class_and_mix(env, rows, X):
+    """Columns whose row-to-row steps span every width class: <= 7 bits (four
+    columns per transpose), 8-15 (pairs), 16-17 (alone), in every mix along a
+    row, so each group size meets each fallback."""
+    torch, daq, oracle = env["torch"], env["daq"], env["oracle"]
+    rng = np.random.default_rng(rows * 7 + X)
+    scale = 2 ** (np.arange(X) * 5 % 17)                     # step sizes 1 .. 65536 across the columns
+    steps = rng.integers(-1, 2, size=(rows, X)) * rng.integers(0, scale + 1, size=(rows, X))
+    pool = (np.cumsum(steps, axis=0) % 65536 - 32768).astype(np.int16)
+    want = oracle.pack(pool)
+    got, n = daq.pack_pool(torch.from_numpy(pool).cuda(), rows)
+    assert n == want.size and np.array_equal(got.cpu().numpy(), want)
+    assert np.array_equal(daq.unpack_pool(got, rows, X).cpu().numpy(), pool)
+    assert np.array_equal(daq.unpack_pool(torch.from_numpy(want).cuda(), rows, X).cpu().numpy(), pool)
+
+
+@pytest.mark.gpu
 def test_full_fill_pool(env):
     torch, daq, oracle = env["torch"], env["daq"], env["oracle"]
     import synth
