@@ -106,7 +106,15 @@ typedef struct daq_island {
  *                     tiles, look back over earlier tiles' states and compact
  *                     each tile from L2 once its prefix is known (rows must be
  *                     16-byte aligned with n_samples % 8 == 0, else the call
- *                     takes the two-pass form).
+ *                     takes the two-pass form);
+ *                -6 = single-read form: one CTA per SM reads every sample from
+ *                     HBM once; the crystal-sum warps write each tile's raw
+ *                     rows into the SM's Tensor Memory, where they wait for the
+ *                     tile's prefix, and the marked ones are then staged and
+ *                     bulk-copied to the pool (the same row and n_xtal
+ *                     conditions as -5, and n_xtal even, else the two-pass
+ *                     form).  The kernel takes all 512 Tensor Memory columns
+ *                     of each SM it runs on for its duration.
  *   stream       cudaStream_t (NULL = legacy default stream).
  *   workspace    device scratch of at least daq_workspace_size() bytes,
  *                16-byte aligned; reused by the call and not to be shared by
@@ -330,8 +338,8 @@ int daq_process_fills_static(const int16_t *samples, int n_calo, int n_xtal, int
  *                and params->grid are ignored and chosen by the tuner.
  *   plan_flags   DAQ_TUNE: time the candidate configurations (two-pass form at
  *                the library's tile and at tile widths 128/224/384/448 with 2 or
- *                1 CTAs per SM; the single-pass forms) on this batch and keep
- *                the fastest.  The choice is remembered per (device, sizes,
+ *                1 CTAs per SM; the single-launch form at 448) on this batch and
+ *                keep the fastest.  The choice is remembered per (device, sizes,
  *                windows, decimation, flags) for the rest of the process.
  *                DAQ_TUNE_FORCE: ignore a remembered choice.
  *   *plan        receives the plan (NULL on error).

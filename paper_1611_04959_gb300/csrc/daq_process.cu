@@ -47,6 +47,7 @@
 #include "daq_steps.cuh"
 #include "daq_twopass.cuh"
 #include "daq_stream.cuh"
+#include "daq_park.cuh"
 
 namespace daq {
 
@@ -667,6 +668,15 @@ static size_t stream_smem(int tw, int X, int slot_bytes, int need_sarr, int nm, 
     }
 }
 
+static size_t park_smem(int tw, int X, int slot_bytes, int need_sarr, int nm, int nc, int np)
+{
+    switch (tw) {
+    case 128: return ParkSmem<128>(X, slot_bytes, need_sarr, nm, nc, np).total;
+    case 224: return ParkSmem<224>(X, slot_bytes, need_sarr, nm, nc, np).total;
+    default: return ParkSmem<448>(X, slot_bytes, need_sarr, nm, nc, np).total;
+    }
+}
+
 static size_t pipe_smem(int tw, int X, int slot_bytes, int rs, int need_sarr)
 {
     switch (tw) {
@@ -710,9 +720,11 @@ struct Plan {
     int tw, hl, hr, ew, rs, boxw, nbox, box_stride, slot_bytes, need_sarr, mode;
     int boxw_b, nbox_b, box_stride_b, slot_bytes_b, rs_b;  // compact pass (two-pass mode)
     size_t smem, smem_b;                                   // tile (or count) kernel, compact kernel
-    int str_meta, str_stages;                              // streaming form: tile records, row stages per CTA
+    int str_meta, str_stages;                              // streaming / single-read forms: tile records, row stages per CTA
+    int pk_slots, pk_cols;                                 // single-read form: park slots, Tensor Memory columns per slot
     int count_ns;                                          // two-pass form: tile slots of the count kernel (2 or 3)
     int64_t max_tiles;
+    int64_t ws_tiles;  // tiles the workspace is laid out for: also covers the two-pass plan a call may fall back to
 };
 
 // Box geometry of `width` samples for the compact pass: nbox boxes of boxw <=
@@ -775,6 +787,28 @@ static void plan_geometry(Plan *pl, int tw, int pre, int post, int X)
             } else break;  // does not fit: make_plan tries a narrower tile
         }
         pl->smem = stream_smem(tw, X, pl->slot_bytes, pl->need_sarr, pl->str_meta, pl->str_stages);
+    } else if (pl->mode == kModePark) {
+        // two out-stages if they fit, else one; then as many tile records as
+        // fit (a multiple of 4); park slots: as many as the Tensor Memory
+        // holds, at most one per tile record
+        const size_t budget = (size_t)kSmemBudget - 1024;
+        pl->pk_cols = park_slot_cols(pl->ew, X);
+        pl->str_stages = kPkMaxOut;
+        pl->str_meta = kPkMaxMeta;
+        auto slots = [&] { return std::max(1, std::min({kPkMaxPark, kPkCols / pl->pk_cols, pl->str_meta})); };
+        for (;;) {
+            pl->pk_slots = slots();
+            if (park_smem(tw, X, pl->slot_bytes, pl->need_sarr, pl->str_meta, pl->str_stages, pl->pk_slots) <= budget)
+                break;
+            if (pl->str_meta > 4) pl->str_meta -= 4;
+            else if (pl->str_stages > 1) {
+                pl->str_stages -= 1;
+                pl->str_meta = kPkMaxMeta;
+            } else break;  // does not fit: make_plan tries a narrower tile
+        }
+        pl->pk_slots = slots();
+        pl->smem = park_smem(tw, X, pl->slot_bytes, pl->need_sarr, pl->str_meta, pl->str_stages, pl->pk_slots);
+        if (pl->pk_cols > kPkCols) pl->smem = (size_t)-1;  // cannot park a tile
     } else if (pl->mode == kModePipelined) {
         pl->smem = pipe_smem(tw, X, pl->slot_bytes, pl->rs, pl->need_sarr);
     } else if (pl->mode == kModePlain) {
@@ -850,7 +884,7 @@ static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, con
     if (n_xtal > kMaxXtal) return DAQ_EUNSUPPORTED;
     if (p->pre < 0 || p->post < 0 || p->pre + p->post > 512 || p->ped_samples < 1) return DAQ_EINVAL;
     if (p->n_decim < 0 || p->n_decim > 2) return DAQ_EINVAL;
-    if (p->grid < -5) return DAQ_EINVAL;
+    if (p->grid < -6) return DAQ_EINVAL;
     if (p->lag_tiles < 0) return DAQ_EINVAL;
     if (p->calo_base < 0 || p->q_calos < 0 ||
         (int64_t)p->calo_base + n_calo > (p->q_calos > 0 ? (int64_t)p->q_calos : (int64_t)n_calo))
@@ -869,6 +903,7 @@ static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, con
                : p->grid == -3 ? kModePipelined
                : p->grid == -4 ? kModeFused
                : p->grid == -5 ? kModeStream
+               : p->grid == -6 ? kModePark
                                : kModePlain;
     const int hl = (p->post + 1 + 7) & ~7, hr = (p->pre + 1 + 7) & ~7;
     const int limit = p->tile ? p->tile : 448;
@@ -898,6 +933,16 @@ static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, con
     if (chosen < 0) return DAQ_EUNSUPPORTED;
     if (chosen != pl->tw) plan_geometry(pl, chosen, p->pre, p->post, n_xtal);
     pl->max_tiles = (int64_t)n_fills * n_calo * ((n_samples + chosen - 1) / chosen);
+    pl->ws_tiles = pl->max_tiles;
+    if (pl->mode == kModeStream || pl->mode == kModePark) {
+        // these forms fall back to the two-pass form at run time when the rows
+        // cannot be bulk-copied (or n_xtal is odd): its tiles may be narrower
+        daq_params q = *p;
+        q.grid = 0;
+        Plan fb;
+        if (make_plan(n_calo, n_xtal, n_samples, n_fills, &q, &fb) == DAQ_OK)
+            pl->ws_tiles = std::max(pl->ws_tiles, fb.max_tiles);
+    }
     return DAQ_OK;
 }
 
@@ -1015,6 +1060,17 @@ template <int TW> static cudaError_t launch_stream(const KArgs &a, const Plan &p
     return cudaGetLastError();
 }
 
+// Single-read form: one persistent CTA per SM (at most one per tile), launched
+// with programmatic stream serialization behind the prepare kernel.
+template <int TW> static cudaError_t launch_park(const KArgs &a, const Plan &pl, int sms, cudaStream_t s)
+{
+    static size_t conf[64] = {0};
+    cudaError_t e = ensure_smem(daq_park_kernel<TW>, pl.smem, conf);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, pl.max_tiles));
+    return launch_pdl(daq_park_kernel<TW>, grid, kPkThreads, pl.smem, s, a);
+}
+
 // Single-launch form: one cooperative launch of every CTA that fits (roles by
 // block).  Events [2], [3] and [4] are all recorded after it.
 template <int TW>
@@ -1074,7 +1130,7 @@ int daq_workspace_size(int n_calo, int n_xtal, int64_t n_samples, int n_fills, c
     Plan pl;
     const int rc = make_plan(n_calo, n_xtal, n_samples, n_fills, params, &pl);
     if (rc) return rc;
-    *bytes = ws_layout(n_fills, n_calo, pl.max_tiles).total;
+    *bytes = ws_layout(n_fills, n_calo, pl.ws_tiles).total;
     return DAQ_OK;
 }
 
@@ -1101,7 +1157,7 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
     for (int d = 0; d < p.n_decim; ++d) q_total += q_bins(n_samples, p.decim[d]) * q_calos;
     if (!skip_q && q_total > 0 && !qhist_inout) return DAQ_EINVAL;
     if (reinterpret_cast<uintptr_t>(out->counts) & 7) return DAQ_EINVAL;
-    const WsLayout wl = ws_layout(n_fills, n_calo, pl.max_tiles);
+    const WsLayout wl = ws_layout(n_fills, n_calo, pl.ws_tiles);
     if (!p.workspace || p.workspace_bytes < wl.total || (reinterpret_cast<uintptr_t>(p.workspace) & 15))
         return DAQ_EINVAL;
 
@@ -1161,9 +1217,10 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
                                strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     }
-    if (pl.mode == kModeStream && !a.use_tma) {
-        // the streaming form reads 16-byte groups and bulk-copies tiles: rows
-        // that are not 16-byte aligned take the two-pass form
+    if ((pl.mode == kModeStream && !a.use_tma) || (pl.mode == kModePark && (!a.use_tma || (n_xtal & 1)))) {
+        // the streaming form reads 16-byte groups and bulk-copies tiles, the
+        // single-read form moves whole 32-bit words of pool rows: rows that
+        // are not 16-byte aligned (or odd crystal counts) take the two-pass form
         daq_params q = p;
         q.grid = 0;
         rc = make_plan(n_calo, n_xtal, n_samples, n_fills, &q, &pl);
@@ -1193,6 +1250,8 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
     a.lag_tiles = std::max<int64_t>(p.lag_tiles > 0 ? p.lag_tiles : kFusedLagTiles, kFusedMinLag);
     a.str_meta = pl.str_meta;
     a.str_stages = pl.str_stages;
+    a.pk_slots = pl.pk_slots;
+    a.pk_cols = pl.pk_cols;
     a.hdr = skip_isl ? nullptr : out->hdr;
     a.hdr_cap = skip_isl ? 0 : out->hdr_cap;
     a.pool = skip_isl ? nullptr : out->pool;
@@ -1231,7 +1290,13 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
 
     const int64_t tiles_cap = std::max<int64_t>(1, std::min<int64_t>(pl.max_tiles, INT32_MAX));
     cudaError_t e;
-    if (pl.mode == kModeStream) {
+    if (pl.mode == kModePark) {
+        switch (pl.tw) {
+        case 128: e = launch_park<128>(a, pl, di.sms, s); break;
+        case 224: e = launch_park<224>(a, pl, di.sms, s); break;
+        default: e = launch_park<448>(a, pl, di.sms, s); break;
+        }
+    } else if (pl.mode == kModeStream) {
         switch (pl.tw) {
         case 128: e = launch_stream<128>(a, pl, di.sms, s); break;
         case 224: e = launch_stream<224>(a, pl, di.sms, s); break;
@@ -1286,7 +1351,7 @@ int64_t daq_trace_tiles(int n_calo, int n_xtal, int64_t n_samples, int n_fills, 
 {
     Plan pl;
     if (make_plan(n_calo, n_xtal, n_samples, n_fills, params, &pl) != DAQ_OK) return 0;
-    return pl.max_tiles;
+    return pl.ws_tiles;
 }
 
 int daq_status_from_counts(const int64_t *c)

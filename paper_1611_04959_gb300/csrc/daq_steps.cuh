@@ -22,7 +22,7 @@ namespace daq {
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // bounded device waits (4 s)
 constexpr int kMaxTileWords = 14;                 // marks words of the widest two-pass tile (448 samples)
 // kernels a call may use (daq_params.grid picks one)
-enum : int32_t { kModeTwoPass = 0, kModePlain = 1, kModePipelined = 2, kModeFused = 3, kModeStream = 4 };
+enum : int32_t { kModeTwoPass = 0, kModePlain = 1, kModePipelined = 2, kModeFused = 3, kModeStream = 4, kModePark = 5 };
 constexpr int kMaxXtal = 64;
 constexpr int kMaxExtBits = 1024;  // tile + halos: one warp of 32-bit words
 
@@ -121,7 +121,8 @@ struct KArgs {
     // single-launch form: tiles the count role may run ahead of the compact
     // role, and the two progress counters (tiles scanned, tiles compacted)
     int64_t lag_tiles;
-    int32_t str_meta, str_stages;  // streaming form: tile records and row stages per CTA
+    int32_t str_meta, str_stages;  // streaming and single-read forms: tile records and row stages per CTA
+    int32_t pk_slots, pk_cols;     // single-read form: Tensor Memory park slots per CTA, columns per slot
     unsigned long long *fctr;
     // outputs
     daq_island *hdr;

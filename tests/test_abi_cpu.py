@@ -75,7 +75,7 @@ def test_tile_choice(daq, pre, post, grid, tile, expect):
 
 @pytest.mark.parametrize("bad", [
     dict(pre=-1), dict(post=-2), dict(ped_samples=0), dict(decim=(0,)), dict(pre=300, post=300),
-    dict(tile=100), dict(grid=-6), dict(lag_tiles=-1), dict(calo_base=-1), dict(q_calos=-1), dict(calo_base=1, q_calos=1),
+    dict(tile=100), dict(grid=-7), dict(lag_tiles=-1), dict(calo_base=-1), dict(q_calos=-1), dict(calo_base=1, q_calos=1),
 ])
 def test_bad_parameters_rejected_before_any_device_work(daq, bad):
     kw = dict(threshold=30, pre=8, post=24, ped_samples=100, decim=(32,))

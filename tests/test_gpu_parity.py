@@ -50,7 +50,7 @@ def test_plain_one_calorimeter_full_fill(env):
 
 
 @pytest.mark.parametrize("tile", [128, 224, 384, 448, 960])
-@pytest.mark.parametrize("grid", [0, -1, -2, -3, -4, -5, 1, 5])
+@pytest.mark.parametrize("grid", [0, -1, -2, -3, -4, -5, -6, 1, 5])
 def test_tile_and_grid_invariance(env, tile, grid):
     from synth import workloads as W
     w = W.scaled(W.PLAIN_FULL_FILL, n_calo=3, n_samples=40_000)
@@ -92,7 +92,7 @@ def test_random_shapes(env, seed):
     hr = (params["pre"] + 8) // 8 * 8
     if tile and tile + hl + hr > 1024:
         tile = 0
-    compare(env, s, params, fill_len=fill_len, tile=tile, grid=int(rng.choice([0, 0, -1, -2, -3, -4, -4, 2, -5, -5])))
+    compare(env, s, params, fill_len=fill_len, tile=tile, grid=int(rng.choice([0, 0, -1, -2, -3, -4, -4, 2, -5, -5, -6, -6, -6])))
 
 
 def test_uneven_batch_of_fills(env):
@@ -103,14 +103,14 @@ def test_uneven_batch_of_fills(env):
     compare(env, s, w.params(), fill_len=fl)
 
 
-@pytest.mark.parametrize("tile", [0, 384, 448])
-def test_stress_parameters(env, tile):
+@pytest.mark.parametrize("tile,grid", [(0, 0), (384, 0), (448, 0), (0, -6)])
+def test_stress_parameters(env, tile, grid):
     """post = 64: the default plan takes 384-sample tiles (two count CTAs per
     SM); 448 runs one count CTA per SM with three tile slots."""
     from synth import workloads as W
     w = W.scaled(W.STRESS, n_fills=2, n_calo=3)
     s = env["synth"].generate(w.config())
-    res, ref = compare(env, s, w.params(), tile=tile)
+    res, ref = compare(env, s, w.params(), tile=tile, grid=grid)
     assert ref["n_rows"] > 0.95 * s.shape[0] * s.shape[1] * s.shape[3]   # heavy merging
 
 
@@ -136,7 +136,7 @@ def test_empty_batch(env):
         assert res["n_islands"] == 0 and res["n_rows"] == 0
 
 
-@pytest.mark.parametrize("grid", [0, -4, -5])
+@pytest.mark.parametrize("grid", [0, -4, -5, -6])
 def test_capacity_overflow_reports_sizes_and_keeps_prefix(env, grid):
     torch, daq, oracle = env["torch"], env["daq"], env["oracle"]
     from synth import workloads as W
@@ -155,7 +155,7 @@ def test_capacity_overflow_reports_sizes_and_keeps_prefix(env, grid):
     assert np.array_equal(q0.cpu().numpy(), ref["q"])          # Q is accumulated exactly once
 
 
-@pytest.mark.parametrize("grid", [0, -4, -5])
+@pytest.mark.parametrize("grid", [0, -4, -5, -6])
 def test_q_accumulates_across_calls_and_skip_flags(env, grid):
     torch, daq, oracle = env["torch"], env["daq"], env["oracle"]
     from synth import workloads as W
@@ -180,19 +180,20 @@ def test_fill_length_out_of_range_is_flagged(env):
     assert e.value.status == daq.DAQ_EINVAL
 
 
-@pytest.mark.parametrize("grid", [0, -4, -5])
+@pytest.mark.parametrize("grid", [0, -4, -5, -6])
 def test_full_fill_24_calorimeters(env, grid):
-    """The benchmark workload itself (1.45 GB), full parity: two-pass, single-launch and streaming forms."""
+    """The benchmark workload itself (1.45 GB), full parity: two-pass, single-launch, streaming and single-read forms."""
     from synth import workloads as W
     w = W.PLAIN_FULL_FILL
     s = env["synth"].generate(w.config())
     compare(env, s, w.params(), n_threads=16, grid=grid)
 
 
-def test_sparse_regime(env):
+@pytest.mark.parametrize("grid", [0, -6])
+def test_sparse_regime(env, grid):
     """Per-crystal noise 3/sqrt(54): islands cover ~8% of the fill."""
     from synth import workloads as W
     w = W.scaled(W.SPARSE_FULL_FILL, n_calo=3)
     s = env["synth"].generate(w.config())
-    res, ref = compare(env, s, w.params())
+    res, ref = compare(env, s, w.params(), grid=grid)
     assert 0.02 < ref["n_rows"] / (3 * s.shape[3]) < 0.2
