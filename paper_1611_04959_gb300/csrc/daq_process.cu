@@ -718,6 +718,7 @@ constexpr int64_t kFusedMinLag = 2 * kCountThreads;
 
 struct Plan {
     int tw, hl, hr, ew, rs, boxw, nbox, box_stride, slot_bytes, need_sarr, mode;
+    int halo_free;  // two-pass form: the count pass loads the tile proper only
     int boxw_b, nbox_b, box_stride_b, slot_bytes_b, rs_b;  // compact pass (two-pass mode)
     size_t smem, smem_b;                                   // tile (or count) kernel, compact kernel
     int str_meta, str_stages;                              // streaming / single-read forms: tile records, row stages per CTA
@@ -755,7 +756,7 @@ static size_t compact_smem_bytes(int tw, int X, int slot_bytes_b)
 
 // Extended tile = nbox TMA boxes of boxw samples: boxw <= 248 and an odd
 // multiple of 8, so a box row (2 boxw bytes) is an odd multiple of 16 bytes.
-static void plan_geometry(Plan *pl, int tw, int pre, int post, int X)
+static void plan_geometry(Plan *pl, int tw, int pre, int post, int X, bool halo_free = false)
 {
     pl->tw = tw;
     pl->hl = (post + 1 + 7) & ~7;
@@ -771,6 +772,16 @@ static void plan_geometry(Plan *pl, int tw, int pre, int post, int X)
     box_geometry(tw, X, &pl->nbox_b, &pl->boxw_b, &pl->box_stride_b);
     pl->rs_b = 2 * pl->boxw_b;
     pl->slot_bytes_b = pl->nbox_b * pl->box_stride_b;
+    pl->halo_free = halo_free;
+    if (pl->halo_free) {  // the count pass reads the same boxes as the compact pass
+        pl->hl = pl->hr = 0;
+        pl->ew = tw;
+        pl->nbox = pl->nbox_b;
+        pl->boxw = pl->boxw_b;
+        pl->rs = pl->rs_b;
+        pl->box_stride = pl->box_stride_b;
+        pl->slot_bytes = pl->slot_bytes_b;
+    }
     pl->smem_b = 0;
     if (pl->mode == kModeStream) {
         // two row stages if they fit, then as many tile records as fit (a
@@ -930,6 +941,28 @@ static int make_plan(int n_calo, int n_xtal, int64_t n_samples, int n_fills, con
             best = cost;
         }
     }
+    if (pl->mode == kModeTwoPass) {
+        // The count pass normally loads each tile with its halo.  Where the
+        // halo forces a narrower tile than allowed, or one count CTA per SM, it
+        // loads the tile proper only (at the widest width) and the scan
+        // completes the marks from the neighbouring tiles' crossings: at the
+        // nominal windows both take the same count time and the completion
+        // costs the scan a few microseconds; with post = 64 the halo-free pass
+        // keeps 448-sample tiles with two count CTAs per SM.
+        int widest = -1;
+        for (int tw : {448, 384, 224, 128})
+            if (tw <= limit) {
+                widest = tw;
+                break;
+            }
+        if (widest > 0) {
+            if (chosen > 0 && chosen != pl->tw) plan_geometry(pl, chosen, p->pre, p->post, n_xtal);
+            if (chosen < 0 || chosen < widest || pl->count_ns == 3) {
+                chosen = widest;
+                plan_geometry(pl, chosen, p->pre, p->post, n_xtal, true);
+            }
+        }
+    }
     if (chosen < 0) return DAQ_EUNSUPPORTED;
     if (chosen != pl->tw) plan_geometry(pl, chosen, p->pre, p->post, n_xtal);
     pl->max_tiles = (int64_t)n_fills * n_calo * ((n_samples + chosen - 1) / chosen);
@@ -1042,7 +1075,7 @@ static cudaError_t launch_twopass(const KArgs &a, const Plan &pl, int grid, int 
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
     const int scan_blocks = (int)((tiles + kScanChunk - 1) / kScanChunk);
-    if ((e = launch_pdl(daq_scan_kernel, scan_blocks, kScanThreads, 0, s, a)) != cudaSuccess) return e;
+    if ((e = launch_pdl(daq_scan_kernel<TW>, scan_blocks, kScanThreads, 0, s, a)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
     if (!skip_isl && (e = launch_pdl(daq_compact_kernel<TW>, grid_b, 256, pl.smem_b, s, a)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[4], s)) != cudaSuccess) return e;
@@ -1246,6 +1279,7 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
                                           pl.boxw_b, n_xtal);
     }
     a.need_sarr = pl.need_sarr;
+    a.halo_free = pl.halo_free;
     a.max_tiles = pl.max_tiles;
     a.lag_tiles = std::max<int64_t>(p.lag_tiles > 0 ? p.lag_tiles : kFusedLagTiles, kFusedMinLag);
     a.str_meta = pl.str_meta;

@@ -111,6 +111,9 @@ struct KArgs {
     int32_t boxw_b, nbox_b, box_stride_b, slot_bytes_b, rs_b;  // compact pass: tile proper only
     int32_t use_tma;
     int32_t mode;
+    // two-pass form: the count pass loads the tile proper only (hl = hr = 0)
+    // and stores internal marks and crossings; the scan completes the marks
+    int32_t halo_free;
     // stage rows: pitch srow bytes = P words, P the first odd number >= ceil(n_xtal/2)
     // (odd, so that the two rows a warp's staging store writes fall in 2-way
     // conflicts at worst); for even n_xtal, wpr = n_xtal/2 words of data per row

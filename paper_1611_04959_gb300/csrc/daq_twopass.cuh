@@ -280,6 +280,24 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
                 break;
             }
             const TileInfo T = tinfo_m[s];
+            if (!kFused && a.halo_free) {
+                // internal marks of the tile and its first / last crossing; the
+                // scan adds the marks that crossings of neighbouring tiles reach
+                const uint32_t A = lane < NWT ? reinterpret_cast<const uint32_t *>(abyte0 + 128 * s)[lane] : 0u;
+                const int nt = (int)(T.t_end - T.t0);
+                const uint32_t Mi = marks_word(a, A, lane) & range_mask(32ll * lane, 0, nt);
+                const unsigned fb = (unsigned)__reduce_min_sync(kFull, A ? (unsigned)(32 * lane + __ffs(A) - 1) : 0xffffffffu);
+                const int lb = (int)__reduce_max_sync(kFull, A ? (unsigned)(32 * lane + 32 - __clz(A)) : 0u) - 1;
+                if (lane < NWT) a.marks[T.tile * NWT + lane] = Mi;
+                if (lane == 0)  // first and last crossing (-1: none), tile within its calorimeter-fill, fill length
+                    *reinterpret_cast<int4 *>(&a.status[T.tile]) =
+                        make_int4(fb != 0xffffffffu ? (int)(T.t0 + fb) : -1, lb >= 0 ? (int)(T.t0 + lb) : -1,
+                                  (int)(T.t0 / TW), (int)T.len);
+                if (!skip_q) q_partial(a, T, blocksum0 + NBT * s, sarr0 + (a.need_sarr ? TW * s : 0), lane, 32);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(mdone + s);
+                continue;
+            }
             unsigned edges;
             const uint32_t Mt = tile_marks<TW>(a, T, abyte0 + 128 * s, &edges, lane);
             const Agg agg = agg_from_marks<TW>(Mt, edges & 1u, (int)(T.t_end - T.t0), lane);
@@ -364,11 +382,85 @@ __device__ __forceinline__ Agg block_scan_incl(Agg v, Agg *warp_tot, Agg *block_
     return v;
 }
 
+// Halo-free count pass: tile j's marks from its internal marks and the
+// threshold crossings of the neighbouring tiles of its calorimeter-fill (a
+// crossing at u marks [u - pre, u + post]: only the last crossing at most post
+// before the tile and the first at most pre after it can reach it).  Stores
+// the completed marks words and returns the tile's record: aggregate, marks of
+// the samples just before and after the tile, marked 64-sample steps.
+template <int TW> __device__ TileRec complete_tile(const KArgs &a, long long j)
+{
+    constexpr int NWT = TW / 32;
+    constexpr int kReach = 4;  // neighbouring tiles read at once on each side
+    const int4 own = *reinterpret_cast<const int4 *>(&a.status[j]);
+    const long long t0 = (long long)own.z * TW, len = own.w;
+    const long long t_end = t0 + TW < len ? t0 + TW : len;
+    const long long cf0 = j - own.z, cf1 = cf0 + (len + TW - 1) / TW;  // tiles of the calorimeter-fill
+    const int nt = (int)(t_end - t0);
+    const long long kNone = 1ll << 40;
+    long long Lp = -kNone, Fn = kNone;  // last crossing before the tile, first after it
+    const int kb = a.post / TW + 1, kf = a.pre / TW + 1;  // tiles a window reaches
+    for (int k0 = 1; k0 <= kb && Lp == -kNone; k0 += kReach) {
+        int l[kReach];
+#pragma unroll
+        for (int u = 0; u < kReach; ++u) {
+            const long long k = j - (k0 + u);
+            l[u] = (k0 + u <= kb && k >= cf0) ? reinterpret_cast<const int2 *>(&a.status[k])->y : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kReach; ++u)
+            if (Lp == -kNone && l[u] >= 0) Lp = l[u];
+    }
+    for (int k0 = 1; k0 <= kf && Fn == kNone; k0 += kReach) {
+        int f[kReach];
+#pragma unroll
+        for (int u = 0; u < kReach; ++u) {
+            const long long k = j + (k0 + u);
+            f[u] = (k0 + u <= kf && k < cf1) ? reinterpret_cast<const int2 *>(&a.status[k])->x : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kReach; ++u)
+            if (Fn == kNone && f[u] >= 0) Fn = f[u];
+    }
+    const long long from_before = Lp + a.post - t0;  // tile columns [0, from_before] are marked from before
+    const long long from_after = Fn - a.pre - t0;    // and [from_after, nt) from after
+    const long long first_at = own.x >= 0 ? own.x : Fn, last_at = own.y >= 0 ? own.y : Lp;
+    const uint32_t m_prev = t0 > 0 && (Lp >= t0 - 1 - a.post || first_at <= t0 - 1 + a.pre);
+    const uint32_t m_next = t_end < len && (last_at >= t_end - a.post || Fn <= t_end + a.pre);
+    uint32_t *mw = a.marks + j * NWT;
+    uint32_t W[NWT];
+#pragma unroll
+    for (int w = 0; w < NWT; ++w) W[w] = mw[w];
+    int m = 0, st = 0, lz = -1;
+    uint32_t steps = 0, below = m_prev;
+#pragma unroll
+    for (int w = 0; w < NWT; ++w) {
+        const long long b = 32ll * w;
+        const uint32_t add = range_mask(b, 0, from_before + 1) | range_mask(b, from_after, nt);
+        const uint32_t Wf = (W[w] | add) & range_mask(b, 0, nt);
+        if (Wf != W[w]) mw[w] = Wf;
+        m += __popc(Wf);
+        st += __popc(Wf & ~((Wf << 1) | below));
+        below = Wf >> 31;
+        const uint32_t zeros = ~Wf & range_mask(b, 0, nt);
+        if (zeros) lz = 32 * w + 31 - __clz(zeros);
+        if (Wf) steps |= 1u << (w >> 1);
+    }
+    TileRec r;
+    r.m = m;
+    r.s = st;
+    r.tr = nt - 1 - lz;
+    r.flags = ((lz < 0 && m_prev) ? 1 : 0) | (int)(m_prev << 1) | (int)(m_next << 2) | (int)(steps << kRecStepShift);
+    return r;
+}
+
 // Single-launch chained scan: blocks take chunks of kScanChunk tiles in ticket
 // order (so every chunk's predecessors are running or done); each reduces its chunk,
 // publishes the aggregate, looks back over earlier chunks' published states
 // for its exclusive prefix (one warp), publishes its inclusive prefix and
-// writes every tile's exclusive prefix.
+// writes every tile's exclusive prefix.  After a halo-free count pass it first
+// completes its tiles' marks and records.
+template <int TW>
 __global__ void __launch_bounds__(kScanThreads) daq_scan_kernel(const __grid_constant__ KArgs a)
 {
     pdl_wait();  // every tile's record
@@ -384,12 +476,16 @@ __global__ void __launch_bounds__(kScanThreads) daq_scan_kernel(const __grid_con
     const long long chunk0 = chunk * kScanChunk;
     if (chunk0 >= total) return;  // grids are sized for the largest tile count
     const long long base = chunk0 + (long long)threadIdx.x * kScanPer;
-    const TileRec *recs = reinterpret_cast<const TileRec *>(a.recs);
+    TileRec *recs = reinterpret_cast<TileRec *>(a.recs);
     TileRec r[kScanPer];
     Agg v = agg_identity();
 #pragma unroll
     for (int i = 0; i < kScanPer; ++i) {
-        r[i] = base + i < total ? recs[base + i] : TileRec{0, 0, 0, 1};
+        if (base + i >= total) r[i] = TileRec{0, 0, 0, 1};
+        else if (a.halo_free) {
+            r[i] = complete_tile<TW>(a, base + i);
+            recs[base + i] = r[i];  // the compact pass reads the completed record and marks
+        } else r[i] = recs[base + i];
         v = combine(v, rec_agg(r[i]));
     }
     Agg blk_tot;

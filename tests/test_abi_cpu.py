@@ -60,8 +60,9 @@ def test_host_calls(daq):
 
 @pytest.mark.parametrize("pre,post,grid,tile,expect", [
     (8, 24, 0, 0, 448),      # nominal windows: 448-sample tiles, two count CTAs per SM
-    (8, 64, 0, 0, 384),      # a 72-sample left halo: two CTAs fit only at 384
-    (8, 64, 0, 448, 448),    # an explicit tile is kept while its plan fits (one CTA per SM)
+    (8, 64, 0, 0, 448),      # the count pass loads no halo, so wide windows keep 448
+    (250, 250, 0, 0, 448),   # windows wider than a 128-sample tile
+    (8, 64, 0, 448, 448),    # an explicit tile is kept while its plan fits
     (8, 64, 0, 384, 384),
     (8, 64, -4, 0, 448),     # other forms: 448 unless it does not fit
     (8, 64, -4, 384, 224),   # 384 is a two-pass width only
