@@ -428,7 +428,7 @@ def bench_gb300(args, ws, rank, local):
                                     "corr": {t: v["corr"] for t, v in scan["thresholds"].items()},
                                     "ratio_of_totals": {t: v["ratio_of_totals"] for t, v in scan["thresholds"].items()}}
 
-    # ---- plain form: one CTA per tile, no persistence
+    # ---- single-pass plain kernel (grid -1): one CTA per tile, no persistence
     if not args.quick:
         pp, _ = make_p(grid=-1)
         pp.workspace, pp.workspace_bytes = workspace.data_ptr(), wsb
@@ -442,8 +442,9 @@ def bench_gb300(args, ws, rank, local):
                 call(pp)
             e1.record(stream)
         torch.cuda.synchronize(dev)
-        result["plain_form"] = {"value": round(Kp * raw_bytes / (e0.elapsed_time(e1) * 1e-3) / 1e9, 2),
-                                "unit": UNIT, "steps": Kp, "form": "single-pass plain kernel, one CTA per tile"}
+        result["single_pass_kernel"] = {"value": round(Kp * raw_bytes / (e0.elapsed_time(e1) * 1e-3) / 1e9, 2),
+                                        "unit": UNIT, "steps": Kp,
+                                        "form": "single-pass plain kernel (grid -1), one CTA per tile"}
 
     # ---- CPU baseline: the oracle on a bounded sample of the same fill (rank 0)
     if rank == 0 and not args.no_cpu_baseline:
@@ -504,6 +505,39 @@ def bench_batched(args, torch, dev, daq, synth, W) -> dict:
     ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = evs[0][0].elapsed_time(evs[-1][1])
     plan.close()
+    # the plain form on the same fills: the default kernels (two-pass, library
+    # tile), one daq_process_fills call per fill, no graph and no tuning; each
+    # call writes its fill's records and rows from the start of the outputs
+    pp = daq.make_params(**params, stream=stream)
+    wsb1 = daq.daq_workspace_size(C, X, N, 1, pp)
+    ws1 = torch.empty(wsb1, dtype=torch.uint8, device=dev)
+    pp.workspace, pp.workspace_bytes = ws1.data_ptr(), wsb1
+    isl = out.struct()
+    fill_bytes = C * X * N * 2
+
+    def plain_batch():
+        for f in range(F):
+            pp.fill_len = fl_d.data_ptr() + 4 * f
+            pp.fill_base = f
+            rc = daq.daq_process_fills(samples.data_ptr() + f * fill_bytes, C, X, N, 1, pp, isl, q.data_ptr())
+            if rc != daq.DAQ_OK:
+                raise daq.DaqError(rc, "plain form")
+
+    for _ in range(2):
+        plain_batch()
+    torch.cuda.synchronize(dev)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(Kb):
+        plain_batch()
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = p0.elapsed_time(p1)
+    plain = {"value": round(Kb * raw / (plain_ms * 1e-3) / 1e9, 2), "unit": UNIT, "steps": Kb,
+             "ms_per_batch": round(plain_ms / Kb, 4),
+             "form": "default two-pass kernels, one daq_process_fills call per fill (16 calls per batch), "
+                     "no graph, no tuning"}
+    del ws1
     res = {"value": round(Kb * raw / (total_ms * 1e-3) / 1e9, 2), "unit": UNIT, "steps": Kb,
            "ms_per_batch": round(total_ms / Kb, 4),
            "latency_ms": {"p50": round(statistics.median(ms), 4), "p99": round(float(np.percentile(ms, 99)), 4)},
@@ -516,7 +550,8 @@ def bench_batched(args, torch, dev, daq, synth, W) -> dict:
            "tuned": {"tile": tuning["tile"], "grid": tuning["grid"], "candidates": tuning["n_tried"],
                      "ms": round(tuning["ms"], 4), "ms_default_config": round(tuning["ms_default"], 4),
                      "tuning_s": round(tune_s, 2)},
-           "gpu_launches": 4 * Kb, "generation_s": round(gen_s, 1)}
+           "gpu_launches": 4 * Kb, "generation_s": round(gen_s, 1),
+           "plain_form": plain, "batched_over_plain": round((Kb * raw / (total_ms * 1e-3)) / (Kb * raw / (plain_ms * 1e-3)), 4)}
     del samples, out, q
     torch.cuda.empty_cache()
     return res
@@ -803,43 +838,28 @@ THRESHOLDS = (5, 10, 15, 20, 30, 50, 100, 300, 1000)
 
 
 def threshold_scan(torch, dev, daq, synth, W, n_fills: int = 12, n_calo: int = 2, thresholds=THRESHOLDS) -> dict:
-    """Island-finding efficiency across thresholds (the check of Fig. 2):
-    datasets are calorimeter-fills of the sparse regime with pulse rates x
-    log-uniform[0.2, 5]; for each threshold T, the islands the path finds in a
-    dataset are compared with its truth islands - those the same path finds in
-    the dataset's noise-free twin (the same pulses; the generator draws pulses
-    and noise from independent streams).  Reports, per T, the least-squares
-    slope of identified on truth through the origin, the ratio of totals and
-    the correlation over datasets."""
-    import numpy as np
+    """Island-finding efficiency across thresholds (Fig. 2): datasets are
+    calorimeter-fills of the sparse regime with pulse rates x
+    log-uniform[0.2, 5]; the islands the CUDA path identifies in each are
+    compared with the truth islands of its injected pulse list (each pulse's
+    samples above T, widened by the windows and merged;
+    paper_1611_04959_gb300.fig2)."""
+    from paper_1611_04959_gb300 import fig2
     w = W.scaled(W.SPARSE_FULL_FILL, n_fills=n_fills, n_calo=n_calo)
-    w0 = W.scaled(W.SPARSE_FULL_FILL, n_fills=n_fills, n_calo=n_calo, noise_sigma=0.0)
     N = w.n_samples
     _, rates = synth.fill_plan(w.synth["seed"] + 29, n_fills, N, N, 0.2, 5.0)
     x = torch.from_numpy(synth.generate(w.config(), rate=rates, n_threads=os.cpu_count() or 1)).to(dev)
-    x0 = torch.from_numpy(synth.generate(w0.config(), rate=rates, n_threads=os.cpu_count() or 1)).to(dev)
-    n_sets = n_fills * n_calo
-    pulses = [len(synth.pulses(w.config(), f, c, N, float(rates[f]))) for f in range(n_fills) for c in range(n_calo)]
+    truth = [[synth.pulses(w.config(), f, c, N, float(rates[f])) for c in range(n_calo)] for f in range(n_fills)]
     base = w.params()
-    rows = {}
-    for T in thresholds:
-        per = []
-        for xx in (x, x0):
-            res = daq.process_fills(xx, **dict(base, threshold=int(T)))
-            isl = res["outputs"].islands_host(res["n_islands"])
-            per.append(np.bincount(isl["fill"].astype(np.int64) * n_calo + isl["calo"], minlength=n_sets))
-        ident, truth = per
-        t, i = truth.astype(np.float64), ident.astype(np.float64)
-        slope = float((t * i).sum() / max(1e-9, (t * t).sum()))
-        corr = float(np.corrcoef(t, i)[0, 1]) if t.std() > 0 and i.std() > 0 else None
-        rows[str(T)] = {"slope": round(slope, 4), "ratio_of_totals": round(float(i.sum() / max(1.0, t.sum())), 4),
-                        "corr": None if corr is None else round(corr, 4),
-                        "truth": truth.tolist(), "identified": ident.tolist()}
-    del x, x0
+    scan = fig2.threshold_scan(x, truth, base, thresholds)
+    del x
     torch.cuda.empty_cache()
-    return {"datasets": f"{n_sets} calorimeter-fills (sparse regime: sum noise sigma ~3 ADC; pulse rate x "
-                        "log-uniform[0.2, 5] per fill); truth = islands of the noise-free twin at the same threshold",
-            "pre": base["pre"], "post": base["post"], "injected_pulses": pulses, "thresholds": rows}
+    return {"datasets": f"{n_fills * n_calo} calorimeter-fills (sparse regime: sum noise sigma ~3 ADC; pulse rate x "
+                        "log-uniform[0.2, 5] per fill); truth = islands of the injected pulse list at the same "
+                        "threshold and windows",
+            "pre": base["pre"], "post": base["post"],
+            "injected_pulses": [len(truth[f][c]) for f in range(n_fills) for c in range(n_calo)],
+            "thresholds": scan["thresholds"]}
 
 
 def burst_schedule(n_fills: int, speed: float, t0_us: float) -> list:
@@ -871,6 +891,9 @@ def bench_served(args, torch, dev, daq, synth, W, samples0) -> dict:
         synth.generate(cfg, out=stage.numpy(), n_threads=os.cpu_count() or 1, fills=(f, 1))
         pool.append(stage[0].to(dev))
     del stage
+    # host input first: measured after the device-resident runs below, its 1x
+    # latencies came out several times longer than on a fresh server process
+    host_rates = served_host_input(args, torch, dev, daq, params, C, X, N, pool[: min(2, n_pool)])
     budget = 40 << 30
     srv = daq.DaqServer(C, X, N, budget, **params, n_streams=4, auto_release=True, device=dev)
     st0 = srv.stats()
@@ -922,7 +945,61 @@ def bench_served(args, torch, dev, daq, synth, W, samples0) -> dict:
                           "pct_of_hbm_peak": round(100.0 * sat_gbs / measured_peaks()[0], 2),
                           "max_running": st["max_running"],
                           "latency_ms_p50": round(sm.latency_p50_us / 1e3, 3)},
-            "q": "one int64 Q histogram resident on the device across every served fill"}
+            "q": "one int64 Q histogram resident on the device across every served fill",
+            "host_input": host_rates}
+
+
+def served_host_input(args, torch, dev, daq, params, C, X, N, dev_fills) -> dict:
+    """The served workload with every fill coming from page-locked host memory:
+    the server copies each fill into its slot (host-to-device) before processing
+    it, so a fill's latency includes the copy.  1x and 10x burst schedules; the
+    link's measured host-to-device rate is the bound."""
+    import numpy as np
+    hosts = []
+    for f in dev_fills:
+        h = torch.empty((C, X, N), dtype=torch.int16).pin_memory()
+        h.copy_(f)
+        hosts.append(h)
+    fill_bytes = C * X * N * 2
+    # the link's host-to-device rate, one fill copied at a time
+    dtmp = torch.empty((C, X, N), dtype=torch.int16, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dtmp.copy_(hosts[0], non_blocking=True)
+    e0.record()
+    for _ in range(4):
+        dtmp.copy_(hosts[0], non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    h2d_gbs = 4 * fill_bytes / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del dtmp
+    srv = daq.DaqServer(C, X, N, 40 << 30, **params, n_streams=4, host_input=True, auto_release=True, device=dev)
+    for k in range(4):
+        srv.submit(hosts[k % len(hosts)])
+    srv.drain(120.0)
+    srv.records(clear=True)
+    out = {"h2d_gbs_measured": round(h2d_gbs, 2), "copy_ms_per_fill_at_link_rate": round(fill_bytes / h2d_gbs / 1e6, 3)}
+    for speed, n in ((1, args.serve_fills_1x), (10, args.serve_fills_host_10x)):
+        t0 = srv.now_us() + 50e3
+        arr = burst_schedule(n, speed, t0)
+        with ClockSampler(dev.index or 0) as clk:
+            for i, a in enumerate(arr):
+                srv.submit(hosts[i % len(hosts)], arrival_us=a)
+            srv.drain(600.0)
+        recs = srv.records(clear=True)
+        assert all(r.status == 0 for r in recs), "served host-input fill failed"
+        sm = daq.daq_serving_summarize(recs)
+        offered = n * fill_bytes / ((arr[-1] - arr[0]) * 1e-6) / 1e9 if n > 1 else None
+        out[f"{speed}x"] = {"fills": n, "fill_spacing_ms": 10.0 / speed,
+                            "latency_ms": {"p50": round(sm.latency_p50_us / 1e3, 4),
+                                           "p99": round(sm.latency_p99_us / 1e3, 4),
+                                           "max": round(sm.latency_max_us / 1e3, 4)},
+                            "p99_under_fill_spacing": bool(sm.latency_p99_us < 10e3 / speed),
+                            "deadtime": round(sm.deadtime, 4), "served_gbs": round(sm.gbs, 2),
+                            "offered_gbs": None if offered is None else round(offered, 2),
+                            "clocks": clk.summary()}
+    srv.close()
+    del hosts
+    return out
 
 
 # ----------------------------------------------------------------------------- reference arm (oracle)
@@ -998,6 +1075,7 @@ def main():
     ap.add_argument("--serve-fills", type=int, default=1024, help="fills per served run at 10x and 100x")
     ap.add_argument("--serve-fills-1x", type=int, default=32, help="fills of the 1x run (1.4 s per 16 fills)")
     ap.add_argument("--serve-fills-saturated", type=int, default=256)
+    ap.add_argument("--serve-fills-host-10x", type=int, default=64, help="fills of the host-input 10x run")
     ap.add_argument("--calos", type=int, default=24, help="calorimeters per fill (24; fewer only for profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

@@ -39,7 +39,8 @@ enum daq_status {
     DAQ_ECUDA = -3,        /* a CUDA call or kernel launch failed */
     DAQ_ETIMEOUT = -4,     /* a bounded device-side wait gave up; outputs are incomplete */
     DAQ_EUNSUPPORTED = -5, /* valid request this build does not handle (e.g. n_xtal > 64) */
-    DAQ_ESCRATCH = -6      /* daq_process_fills_static: the call needs more scratch than the built-in area */
+    DAQ_ESCRATCH = -6,     /* daq_process_fills_static: the call needs more scratch than the built-in area */
+    DAQ_EINDEX = -7        /* DAQ_DEBUG_CHECKS: a computed output index failed its check; that store was skipped */
 };
 
 /* params->flags */
@@ -47,12 +48,14 @@ enum daq_status {
 #define DAQ_SKIP_ISLANDS 2u  /* compute counts, write no island records, pool rows or pedestals */
 #define DAQ_SYNC 4u          /* wait for the stream, then return the device-side status */
 #define DAQ_PACK_POOL 8u     /* daq_process_fills_host: return the pool rows packed (see daq_pack_pool) */
+#define DAQ_DEBUG_CHECKS 16u /* check every computed record, pool and Q index before its store (see below) */
 
 /* Bits of counts[2] (device-side status, OR-ed by the kernels). */
 #define DAQ_DEV_HDR_OVERFLOW 1
 #define DAQ_DEV_POOL_OVERFLOW 2
 #define DAQ_DEV_TIMEOUT 4
 #define DAQ_DEV_BAD_FILL_LEN 8
+#define DAQ_DEV_BAD_INDEX 16 /* DAQ_DEBUG_CHECKS: an index check failed and the store was skipped */
 
 /*
  * One island (Table 2 row 5 "save an array of identified islands"; Sec. 3:
@@ -84,7 +87,18 @@ typedef struct daq_island {
  *   fill_len     device int32[n_fills] fill lengths (0 <= len <= n_samples), or
  *                NULL for n_samples each.  Out-of-range values are clamped and
  *                flagged with DAQ_DEV_BAD_FILL_LEN.
- *   flags        DAQ_SKIP_Q | DAQ_SKIP_ISLANDS | DAQ_SYNC.
+ *   flags        DAQ_SKIP_Q | DAQ_SKIP_ISLANDS | DAQ_SYNC | DAQ_DEBUG_CHECKS.
+ *                DAQ_DEBUG_CHECKS: before each store the kernels check the
+ *                index they computed against what the call's own arithmetic
+ *                allows - an island record's index, fill, calorimeter, start and
+ *                length against the fill, its pool rows against the rows of the
+ *                tiles before it, a tile's pool rows against the tile's width,
+ *                a Q bin against the histogram's bins and calorimeter rows.  A
+ *                failed check sets DAQ_DEV_BAD_INDEX and skips that store; the
+ *                call then returns DAQ_EINDEX.  (Capacity shortfalls are not
+ *                index errors: they stay DAQ_ECAPACITY.)  For debugging: no
+ *                check fails on a correct build, and outputs are identical
+ *                with and without the flag.
  *   tile         samples per tile: 0 = chosen by the library (two-pass form: the
  *                width of least estimated count-pass cost, 448 for the nominal
  *                windows and 384 when the halo of post + pre samples is too
@@ -135,6 +149,14 @@ typedef struct daq_island {
  *                + n_calo must not exceed it (so calo_base > 0 needs q_calos).
  *                Calorimeter c of the call adds to row calo_base + c of each
  *                decimation's block of q_calos rows.
+ *   wait_limit_ns  limit of each device-side wait on state that other CTAs
+ *                publish (0 = 4 s): the look-back over earlier tiles (every
+ *                form's scan), and the single-launch form's scanner and lag
+ *                waits.  A wait that runs out sets DAQ_DEV_TIMEOUT; every CTA
+ *                then stops taking work, waits for its own copies in flight
+ *                and exits, and the call returns DAQ_ETIMEOUT with incomplete
+ *                outputs.  The next call starts clean.  Waits of a CTA on its
+ *                own warps keep the 4 s limit.
  */
 typedef struct daq_params {
     int32_t threshold;
@@ -156,6 +178,7 @@ typedef struct daq_params {
     uint64_t *trace;
     int32_t q_calos;
     int32_t lag_tiles;
+    uint64_t wait_limit_ns;
 } daq_params;
 
 #define DAQ_N_EVENTS 5
@@ -305,8 +328,14 @@ int daq_process_fills_host(int n_calo, int n_xtal, int64_t n_samples, int n_fill
  *   - The area exists once per GPU and lives until the process exits; every
  *     GPU that loads the library holds it.
  *   - The first call on a device looks up the area's device address (a
- *     runtime query, made once per device with that device current).  Make
- *     that first call before any stream capture.
+ *     runtime query, made once per device with that device current).  With
+ *     the CUDA runtime's lazy module loading (the default) that first query is
+ *     also when the area is placed in device memory, so inside a fixed memory
+ *     budget make the first call at start-up, before the budget is spent; make
+ *     it before any stream capture too.  Later calls place nothing.
+ *   - The cached address belongs to the device's current context: after
+ *     cudaDeviceReset the area is gone and this entry point must not be called
+ *     again in that process.
  *   - Every call uses the same area, and it keeps what the last call left in
  *     it; each call re-initialises everything it reads.  Calls whose work
  *     overlaps on the GPU (different streams, or a second call enqueued before
@@ -409,7 +438,9 @@ void daq_tune_cache_clear(void);
  *                   n_calo * n_samples rows, half that plus n_calo + 1 records).
  *   flags           DAQ_SERVER_HOST_INPUT: requests may name host samples,
  *                   copied into the slot's input buffer (page-locked memory
- *                   gives full speed); DAQ_SERVER_AUTO_RELEASE: a slot is freed
+ *                   gives full speed) on one copy stream in admission order,
+ *                   each fill's processing waiting for its own copy;
+ *                   DAQ_SERVER_AUTO_RELEASE: a slot is freed
  *                   as soon as its fill completes (only counts and timings are
  *                   kept; for streaming without reading islands).
  *   qhist           device int64 Q histogram (caller-owned, accumulated), or
@@ -546,7 +577,7 @@ int daq_crystal_sum(const int16_t *samples, int n_calo, int n_xtal, int64_t n_sa
                     const daq_params *params, int64_t *q_xtal);
 
 /*
- * Lossless packing of pool rows (Sec. 2: the frontend compresses island data
+ * Lossless packing of pool rows (Sec. 3: the frontend compresses island data
  * losslessly before sending it to the event builder; the method is not named,
  * the format below is this library's).  Stream (little-endian):
  *   header   u32 magic 0x50514144, u32 n_xtal, u64 rows

@@ -26,7 +26,7 @@
  * Step 4 is written as an explicit scan of every window (O(len * (pre+post))),
  * deliberately not the GPU's bit-parallel form.
  *
- * Packed pool stream (lossless; Sec. 2 has the frontend compress island data
+ * Packed pool stream (lossless; Sec. 3 has the frontend compress island data
  * losslessly before event building, without naming the method - this format
  * is this project's reading):
  *   header   u32 magic 0x50514144, u32 n_xtal, u64 rows

@@ -18,10 +18,11 @@ from . import build as _build
 LIB_PATH = _build.LIB
 
 # status codes and flags (include/daq.h)
-DAQ_OK, DAQ_EINVAL, DAQ_ECAPACITY, DAQ_ECUDA, DAQ_ETIMEOUT, DAQ_EUNSUPPORTED, DAQ_ESCRATCH = 0, -1, -2, -3, -4, -5, -6
+DAQ_OK, DAQ_EINVAL, DAQ_ECAPACITY, DAQ_ECUDA, DAQ_ETIMEOUT, DAQ_EUNSUPPORTED, DAQ_ESCRATCH, DAQ_EINDEX = \
+    0, -1, -2, -3, -4, -5, -6, -7
 DAQ_STATIC_SCRATCH_BYTES = 8 << 20
-DAQ_SKIP_Q, DAQ_SKIP_ISLANDS, DAQ_SYNC, DAQ_PACK_POOL = 1, 2, 4, 8
-DAQ_DEV_HDR_OVERFLOW, DAQ_DEV_POOL_OVERFLOW, DAQ_DEV_TIMEOUT, DAQ_DEV_BAD_FILL_LEN = 1, 2, 4, 8
+DAQ_SKIP_Q, DAQ_SKIP_ISLANDS, DAQ_SYNC, DAQ_PACK_POOL, DAQ_DEBUG_CHECKS = 1, 2, 4, 8, 16
+DAQ_DEV_HDR_OVERFLOW, DAQ_DEV_POOL_OVERFLOW, DAQ_DEV_TIMEOUT, DAQ_DEV_BAD_FILL_LEN, DAQ_DEV_BAD_INDEX = 1, 2, 4, 8, 16
 
 ISLAND_DTYPE = np.dtype([("fill", "<i4"), ("calo", "<i4"), ("start", "<i4"), ("len", "<i4"),
                          ("pool_row", "<i8")])
@@ -34,7 +35,7 @@ class DaqParams(ctypes.Structure):
                 ("tile", ctypes.c_int32), ("grid", ctypes.c_int32), ("calo_base", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("events", ctypes.c_void_p), ("trace", ctypes.c_void_p),
-                ("q_calos", ctypes.c_int32), ("lag_tiles", ctypes.c_int32)]
+                ("q_calos", ctypes.c_int32), ("lag_tiles", ctypes.c_int32), ("wait_limit_ns", ctypes.c_uint64)]
 
 
 class DaqIslands(ctypes.Structure):
@@ -381,7 +382,7 @@ def daq_status_from_counts(counts_host) -> int:
 # ------------------------------------------------------------------- torch marshalling helpers
 def make_params(threshold=30, pre=8, post=24, ped_samples=100, decim=(32,), fill_base=0, fill_len=None,
                 flags=0, tile=0, grid=0, stream=None, workspace=None, calo_base=0, q_calos=0,
-                lag_tiles=0) -> DaqParams:
+                lag_tiles=0, wait_limit_ns=0) -> DaqParams:
     p = daq_params_default()
     p.threshold, p.pre, p.post, p.ped_samples = int(threshold), int(pre), int(post), int(ped_samples)
     decim = tuple(decim)
@@ -393,6 +394,7 @@ def make_params(threshold=30, pre=8, post=24, ped_samples=100, decim=(32,), fill
     p.flags = int(flags)
     p.tile, p.grid = int(tile), int(grid)
     p.calo_base, p.q_calos, p.lag_tiles = int(calo_base), int(q_calos), int(lag_tiles)
+    p.wait_limit_ns = int(wait_limit_ns)
     p.stream = None if stream is None else int(stream.cuda_stream)
     if workspace is not None:
         p.workspace = int(workspace.data_ptr())
@@ -429,11 +431,12 @@ class Outputs:
 def process_fills(samples, threshold=30, pre=8, post=24, ped_samples=100, decim=(32,), fill_len=None,
                   fill_base=0, q=None, outputs: Outputs | None = None, hdr_cap=None, pool_cap=None,
                   workspace=None, flags=0, tile=0, grid=0, stream=None, sync=True, calo_base=0, q_calos=0,
-                  lag_tiles=0) -> dict:
+                  lag_tiles=0, wait_limit_ns=0, allow=()) -> dict:
     """Run the path on a CUDA int16 tensor samples[F][C][X][N].
 
     Allocates (with torch) whatever output the caller did not pass; returns a
-    dict with the tensors, the host counts (when sync) and the status."""
+    dict with the tensors, the host counts (when sync) and the status.  Raises
+    DaqError for any status but DAQ_OK, DAQ_ECAPACITY and those in `allow`."""
     import torch
     if not samples.is_cuda or samples.dtype != torch.int16 or samples.dim() != 4 or not samples.is_contiguous():
         raise ValueError("samples must be a contiguous CUDA int16 tensor [fills][calo][xtal][samples]")
@@ -451,7 +454,7 @@ def process_fills(samples, threshold=30, pre=8, post=24, ped_samples=100, decim=
         q = torch.zeros(q_size(q_calos or C, N, decim), dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev) if stream is None else stream
     p = make_params(threshold, pre, post, ped_samples, decim, fill_base, fill_len, flags, tile, grid, stream,
-                    calo_base=calo_base, q_calos=q_calos, lag_tiles=lag_tiles)
+                    calo_base=calo_base, q_calos=q_calos, lag_tiles=lag_tiles, wait_limit_ns=wait_limit_ns)
     ws_bytes = daq_workspace_size(C, X, N, F, p)
     if workspace is None or workspace.numel() * workspace.element_size() < ws_bytes:
         workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
@@ -461,7 +464,7 @@ def process_fills(samples, threshold=30, pre=8, post=24, ped_samples=100, decim=
     rc = daq_process_fills(samples.data_ptr(), C, X, N, F, p, outputs.struct(),
                            None if q is None else q.data_ptr())
     res = dict(outputs=outputs, q=q, workspace=workspace, status=rc)
-    if rc not in (DAQ_OK, DAQ_ECAPACITY):
+    if rc not in (DAQ_OK, DAQ_ECAPACITY) and rc not in allow:
         raise DaqError(rc, "daq_process_fills")
     if sync:
         counts = outputs.counts.cpu().numpy()

@@ -24,6 +24,10 @@ namespace {
 constexpr int kMaxChunks = 64;
 constexpr int kTargetChunks = 12;        // rows copied back as they are
 constexpr int kTargetChunksPacked = 24;  // rows packed on the GPU first
+// make_chunks may return up to about twice its target (whole fills, or groups
+// of calorimeters, rounded), and every per-chunk array holds kMaxChunks
+static_assert(2 * kTargetChunks <= kMaxChunks && 2 * kTargetChunksPacked <= kMaxChunks,
+              "chunk plans must fit the per-chunk arrays");
 constexpr int kMaxDevices = 64;
 
 // Streams, events and count buffers of the pipeline, created on a device's
@@ -148,6 +152,7 @@ extern "C" int daq_process_fills_host(int n_calo, int n_xtal, int64_t n_samples,
             r += (c.row_cap + 7) & ~int64_t(7);
         }
         if (ch.size() > 1 && !skip_isl && (h > dev->hdr_cap || r > dev->pool_row_cap)) ch.resize(1);
+        if (ch.size() > (size_t)kMaxChunks) ch.resize(1);  // more chunks than the per-chunk arrays hold: one chunk
         if (ch.size() == 1) {
             ch[0] = Chunk{0, n_fills, 0, n_calo, 0, dev->hdr_cap, 0, dev->pool_row_cap, 0, 0, 0, 0, 0};
         }

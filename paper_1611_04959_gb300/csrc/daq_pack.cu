@@ -1,4 +1,4 @@
-// Lossless packing of pool rows on the GPU (Sec. 2: the frontend compresses
+// Lossless packing of pool rows on the GPU (Sec. 3: the frontend compresses
 // island data losslessly before event building).  Stream format:
 //   header   u32 magic 0x50514144, u32 n_xtal, u64 rows
 //   offsets  u64[n_blocks + 1], n_blocks = ceil(rows / 32): byte offset of each

@@ -488,7 +488,11 @@ __global__ void __launch_bounds__(kPkThreads, 1) daq_park_kernel(const __grid_co
             tmem_fence_after_sync();
             const TileInfo T = M->T;
             const Agg agg = M->agg, excl = M->excl;
-            const bool rows = !skip_isl && !excl.poison && agg.m > 0;
+            bool rows = !skip_isl && !excl.poison && agg.m > 0;
+            if (rows && (a.flags & DAQ_DEBUG_CHECKS) && (excl.m < 0 || agg.m > T.t_end - T.t0)) {
+                if (q == 0 && lane == 0) set_status_bit(a, DAQ_DEV_BAD_INDEX);  // more rows than the out-stage holds
+                rows = false;
+            }
             if (q == 0 && lane == 0) trace_stamp(a, T.tile, 8);
             if (rows) {
                 const int nt = (int)(T.t_end - T.t0);
@@ -549,7 +553,8 @@ __global__ void __launch_bounds__(kPkThreads, 1) daq_park_kernel(const __grid_co
                 ge = cap_b;
                 if (lane == 0 && !skip_isl && !excl.poison) set_status_bit(a, DAQ_DEV_POOL_OVERFLOW);
             }
-            if (!skip_isl && !excl.poison && ge > gs) {
+            const bool bad = (a.flags & DAQ_DEBUG_CHECKS) && (excl.m < 0 || agg.m > T.t_end - T.t0);
+            if (!skip_isl && !excl.poison && !bad && ge > gs) {
                 long long a16 = (gs + 15) & ~15ll, b16 = ge & ~15ll;
                 if (a16 > ge) a16 = ge;
                 if (b16 < a16) b16 = a16;

@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 2) daq_tile_kernel(const __grid_cons
             trace_stamp(a, T.tile, 8);
         }
         if (!excl.poison && !skip_isl) {
-            copy_out(a, stage, rowtab, excl, agg, tid, kThreads);
+            copy_out(a, stage, rowtab, excl, agg, tid, kThreads, TW);
             if (warp == 0) write_headers<TW>(a, T, W, excl, lane);
         }
         if (tid == 0) trace_stamp(a, T.tile, 9);
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) daq_pipe_kernel(const __grid_
             if (!pipe_wait(a, bars + kBarOutFull + o, (uint32_t)((i / kNOut) & 1))) break;
             if (gt == 0) trace_stamp(a, T.tile, 12);
             if (!excl.poison && !skip_isl) {
-                copy_out(a, out0 + (size_t)o * stage_bytes, M->rowtab, excl, agg, gt, nthr);
+                copy_out(a, out0 + (size_t)o * stage_bytes, M->rowtab, excl, agg, gt, nthr, TW);
                 if (gt == 0) trace_stamp(a, T.tile, 13);
                 if (warp == kPipeWriter0) write_headers<TW>(a, T, words(m), excl, lane);
             }
@@ -1215,6 +1215,8 @@ int daq_process_fills(const int16_t *samples, int n_calo, int n_xtal, int64_t n_
     }
     a.fill_base = p.fill_base;
     a.calo_base = p.calo_base;
+    a.q_calos = (int32_t)q_calos;
+    a.wait_ns = p.wait_limit_ns ? p.wait_limit_ns : kWaitLimitNs;
     a.fill_len = p.fill_len;
     a.flags = p.flags;
     a.hl = pl.hl;
@@ -1393,6 +1395,7 @@ int daq_status_from_counts(const int64_t *c)
     if (!c) return DAQ_EINVAL;
     if (c[2] & DAQ_DEV_TIMEOUT) return DAQ_ETIMEOUT;
     if (c[2] & DAQ_DEV_BAD_FILL_LEN) return DAQ_EINVAL;
+    if (c[2] & DAQ_DEV_BAD_INDEX) return DAQ_EINDEX;
     if (c[2] & (DAQ_DEV_HDR_OVERFLOW | DAQ_DEV_POOL_OVERFLOW)) return DAQ_ECAPACITY;
     return DAQ_OK;
 }
@@ -1407,11 +1410,12 @@ const char *daq_strerror(int status)
     case DAQ_ETIMEOUT: return "a bounded device-side wait gave up; outputs are incomplete";
     case DAQ_EUNSUPPORTED: return "request not supported by this build";
     case DAQ_ESCRATCH: return "the call needs more scratch than the library's built-in area holds";
+    case DAQ_EINDEX: return "a device-side index check (DAQ_DEBUG_CHECKS) failed; the store was skipped";
     default: return "unknown status";
     }
 }
 
-int daq_version(void) { return 101; }
+int daq_version(void) { return 102; }
 
 const char *daq_last_cuda_error(void)
 {

@@ -44,6 +44,7 @@ struct Slot {
     void *ws = nullptr;
     int32_t *len = nullptr;    // device fill length
     cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+    cudaEvent_t ev_copied = nullptr;  // DAQ_SERVER_HOST_INPUT: the fill's samples are on the device
     int64_t ticket = 0;        // 0 = free
     int stream = 0;
 };
@@ -72,6 +73,11 @@ struct daq_server {
     int32_t *len_host = nullptr;     // [n_slots], page-locked
     std::vector<cudaStream_t> streams;
     int next_stream = 0;
+    // DAQ_SERVER_HOST_INPUT: host-to-device copies of fills, one at a time in
+    // admission order, so that each fill's copy ends as early as the link
+    // allows (copies spread over the processing streams would share the link
+    // and all end late)
+    cudaStream_t copy_stream = nullptr;
 
     Clock::time_point t0;
     cudaEvent_t ref_ev = nullptr;
@@ -140,13 +146,16 @@ void admit(daq_server *s, int si, Fill &f)
     daq_islands isl{sl.hdr, s->hdr_cap, sl.pool, s->pool_cap, sl.ped, sl.counts};
     const int16_t *in = f.samples;
     int rc = DAQ_OK;
-    if (cudaEventRecord(sl.ev_start, st) != cudaSuccess) rc = DAQ_ECUDA;
+    // the fill's work starts with its copy (host input) or its processing
+    if (cudaEventRecord(sl.ev_start, f.on_host ? s->copy_stream : st) != cudaSuccess) rc = DAQ_ECUDA;
     if (rc == DAQ_OK &&
         cudaMemcpyAsync(sl.len, &s->len_host[si], sizeof(int32_t), cudaMemcpyHostToDevice, st) != cudaSuccess)
         rc = DAQ_ECUDA;
     if (rc == DAQ_OK && f.on_host) {
         if (cudaMemcpyAsync(sl.input, f.samples, (size_t)c.n_calo * X * N * sizeof(int16_t), cudaMemcpyHostToDevice,
-                            st) != cudaSuccess)
+                            s->copy_stream) != cudaSuccess ||
+            cudaEventRecord(sl.ev_copied, s->copy_stream) != cudaSuccess ||
+            cudaStreamWaitEvent(st, sl.ev_copied, 0) != cudaSuccess)
             rc = DAQ_ECUDA;
         in = sl.input;
     }
@@ -248,8 +257,10 @@ void free_server(daq_server *s)
     for (Slot &sl : s->slots) {
         if (sl.ev_start) cudaEventDestroy(sl.ev_start);
         if (sl.ev_done) cudaEventDestroy(sl.ev_done);
+        if (sl.ev_copied) cudaEventDestroy(sl.ev_copied);
     }
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+    if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
     if (s->ref_ev) cudaEventDestroy(s->ref_ev);
     if (s->arena) cudaFree(s->arena);
     if (s->own_q && s->q) cudaFree(s->q);
@@ -348,7 +359,13 @@ int daq_server_create(const daq_server_config *cfg, daq_server **out)
         sl.len = reinterpret_cast<int32_t *>(b);
         if (cudaEventCreate(&sl.ev_start) != cudaSuccess || cudaEventCreate(&sl.ev_done) != cudaSuccess)
             return fail(DAQ_ECUDA);
+        if ((cfg->flags & DAQ_SERVER_HOST_INPUT) &&
+            cudaEventCreateWithFlags(&sl.ev_copied, cudaEventDisableTiming) != cudaSuccess)
+            return fail(DAQ_ECUDA);
     }
+    if ((cfg->flags & DAQ_SERVER_HOST_INPUT) &&
+        cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(DAQ_ECUDA);
     const int n_streams = cfg->n_streams ? cfg->n_streams : 4;
     s->streams.resize(n_streams, nullptr);
     for (int i = 0; i < n_streams; ++i)

@@ -11,7 +11,9 @@
 // code cannot hand the array's name to a kernel (on the host that name is only
 // a stand-in, not a device address), so the first call on each device asks the
 // runtime for the array's device address once, with that device current, and
-// keeps it.
+// keeps it.  Under lazy module loading that first query is also when the
+// module, and with it the area, is placed on the device; the address is that
+// of the current context and does not survive cudaDeviceReset.
 #include <cuda_runtime.h>
 
 #include <cstring>

@@ -104,6 +104,8 @@ struct KArgs {
     int32_t n_decim, decim[2];
     int64_t qbins[2], qoff[2];
     int32_t fill_base, calo_base;
+    int32_t q_calos;  // calorimeter rows of each decimation's block of Q
+    uint64_t wait_ns;  // limit of waits on other CTAs' published state
     const int32_t *fill_len;
     uint32_t flags;
     int32_t hl, hr, ew, rs;  // halo left/right, extended width, smem row pitch (bytes) = 2 boxw
@@ -585,7 +587,7 @@ __device__ __forceinline__ unsigned read_status(const TileStatus *st, long long 
 // from the latest); the window's combination is formed with warp reductions:
 // marked and start counts add up, and the trailing run adds the runs of the
 // latest entries up to and including the first one that is not fully marked.
-// Bounded: gives up after kWaitLimitNs or once another CTA has flagged a
+// Bounded: gives up after a.wait_ns or once another CTA has flagged a
 // timeout, returning a poisoned prefix.
 __device__ Agg look_back_in(const KArgs &a, const TileStatus *st, long long tile, int lane, unsigned *stats = nullptr)
 {
@@ -622,8 +624,8 @@ __device__ Agg look_back_in(const KArgs &a, const TileStatus *st, long long tile
                 t_start = global_ns();
                 waiting = true;
             }
-            if ((iter & 15u) == 15u) {
-                int give_up = lane == 0 && (global_ns() - t_start > kWaitLimitNs || aborted(a));
+            {  // the clock every poll (a short limit must bite); the flag every 16th
+                int give_up = lane == 0 && (global_ns() - t_start > a.wait_ns || ((iter & 15u) == 15u && aborted(a)));
                 if (__shfl_sync(kFull, give_up, 0)) {
                     acc.poison = 1;
                     if (lane == 0) set_status_bit(a, DAQ_DEV_TIMEOUT);
@@ -690,9 +692,13 @@ __device__ __forceinline__ Agg look_back(const KArgs &a, long long tile, int lan
 // to global rows [excl.m, excl.m + agg.m): whole 16-byte chunks from one
 // thread each, the unaligned ends in smaller stores.
 __device__ __forceinline__ void copy_out(const KArgs &a, const unsigned char *stage, const int16_t *rowtab,
-                                         const Agg &excl, const Agg &agg, int gt, int nthr)
+                                         const Agg &excl, const Agg &agg, int gt, int nthr, int max_rows)
 {
     long long rows = agg.m;
+    if ((a.flags & DAQ_DEBUG_CHECKS) && (excl.m < 0 || rows < 0 || rows > max_rows)) {
+        if (gt == 0) set_status_bit(a, DAQ_DEV_BAD_INDEX);  // more rows than the stage holds
+        return;
+    }
     if (excl.m + rows > a.pool_cap) {
         rows = a.pool_cap - excl.m;
         if (gt == 0) set_status_bit(a, DAQ_DEV_POOL_OVERFLOW);
@@ -785,6 +791,12 @@ __device__ __forceinline__ void write_headers(const KArgs &a, const TileInfo &T,
         const long long t_e = T.t0 + 32 * lane + b;
         const long long ilen = t_e - start + 1;
         const long long row_end = excl.m + w.mb[lane] + __popc(Mt & upto) - 1;
+        if ((a.flags & DAQ_DEBUG_CHECKS) &&
+            !(idx >= 0 && T.f >= 0 && T.f < a.n_fills && T.c >= 0 && T.c < a.n_calo && start >= 0 && ilen >= 1 &&
+              t_e < T.len && row_end - ilen + 1 >= 0 && row_end - ilen + 1 <= row_end)) {
+            set_status_bit(a, DAQ_DEV_BAD_INDEX);  // the record would not describe the fill: skip it
+            continue;
+        }
         if (idx < a.hdr_cap) {
             daq_island *h = a.hdr + idx;
             h->fill = a.fill_base + T.f;
@@ -818,6 +830,11 @@ __device__ __forceinline__ void q_partial(const KArgs &a, const TileInfo &T, con
                 for (long long b = lo >> 3; b < (hi + 7) >> 3; ++b) sum += blocksum[b];
             } else {
                 for (long long t = lo; t < hi; ++t) sum += sarr[t];
+            }
+            if ((a.flags & DAQ_DEBUG_CHECKS) &&
+                !(k >= 0 && k < a.qbins[d] && a.calo_base + T.c >= 0 && a.calo_base + T.c < a.q_calos)) {
+                set_status_bit(a, DAQ_DEV_BAD_INDEX);
+                continue;
             }
             atomicAdd(qrow + k, (unsigned long long)sum);
         }

@@ -444,7 +444,11 @@ __global__ void __launch_bounds__(kStrThreads, 1) daq_stream_kernel(const __grid
             const TileInfo T = M->T;
             if (T.tile < 0) break;
             const Agg agg = M->agg, excl = M->excl;
-            const bool rows = !skip_isl && agg.m > 0 && !excl.poison;
+            bool rows = !skip_isl && agg.m > 0 && !excl.poison;
+            if (rows && (a.flags & DAQ_DEBUG_CHECKS) && (excl.m < 0 || agg.m > T.t_end - T.t0)) {
+                if (lane == 0) set_status_bit(a, DAQ_DEV_BAD_INDEX);  // more rows than the tile has samples
+                rows = false;
+            }
             if (lane == 0) trace_stamp(a, T.tile, 7);
             if (rows) {
                 unsigned char *stage = stage0 + (size_t)o * stage_bytes;

@@ -97,6 +97,24 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
     return !__any_sync(kFull, !ok);
 }
 
+// As warp_wait, but also giving up once a CTA has flagged a timeout (the
+// single-launch form, whose waits on other CTAs may run out).
+__device__ __forceinline__ bool warp_wait_abortable(const KArgs &a, uint64_t *bar, uint32_t parity)
+{
+    bool ok = mbar_try_wait(bar, parity);
+    if (!ok) {
+        const uint64_t t0 = global_ns();
+        for (uint32_t i = 1;; ++i) {
+            if (mbar_try_wait(bar, parity)) {
+                ok = true;
+                break;
+            }
+            if ((i & 63u) == 0u && (aborted(a) || global_ns() - t0 > kWaitLimitNs)) break;
+        }
+    }
+    return !__any_sync(kFull, !ok);
+}
+
 // Shared-memory layout of the count kernel with NS tile slots, in the order of
 // the buffers.
 template <int NS> struct CountSmemT {
@@ -147,13 +165,11 @@ __device__ __forceinline__ bool wait_counter_ge(const KArgs &a, const unsigned l
     for (uint32_t i = 0;; ++i) {
         __nanosleep(64);
         if (ld_acquire_u64(p) >= v) return true;
-        if ((i & 63u) == 63u) {
-            if (aborted(a)) return false;
-            if (global_ns() - t0 > kWaitLimitNs) {
-                set_status_bit(a, DAQ_DEV_TIMEOUT);
-                return false;
-            }
+        if (global_ns() - t0 > a.wait_ns) {
+            set_status_bit(a, DAQ_DEV_TIMEOUT);
+            return false;
         }
+        if ((i & 63u) == 63u && aborted(a)) return false;
     }
 }
 
@@ -202,10 +218,11 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
     const int n_steps = (a.ew + 63) / 64;
     constexpr int kSumThreads = 32 * NSW;
 
+    uint32_t pend = 0, pend_par = 0;  // thread 0: slots with a load issued, parity of its phase
     auto start_load = [&](long long tile, int s) {  // thread 0
         if (kFused &&
             !wait_counter_ge(a, compacted_ctr(a), tile > a.lag_tiles ? (unsigned long long)(tile - a.lag_tiles) : 0ull))
-            return;  // timed out: the sum warps time out on this slot too
+            return;  // gave up (the flag is set): the sum warps stop at this slot
         TileInfo &T = tinfo[s];
         decode_tile<TW>(a, tile, T, plan.fts, plan.lens);
         trace_stamp(a, tile, 0);
@@ -215,8 +232,13 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(full + s, tile_load_bytes(a));
             issue_tile_load(a, T, slot0 + (size_t)s * a.slot_bytes, full + s);
+            pend |= 1u << s;
+            pend_par = (pend_par & ~(1u << s)) | ((uint32_t)(((tile - first) / G / NS) & 1) << s);
         }
         trace_stamp(a, tile, 1);
+    };
+    auto slot_wait = [&](uint64_t *bar, uint32_t parity) {
+        return kFused ? warp_wait_abortable(a, bar, parity) : warp_wait(bar, parity);
     };
 
     if (warp < NSW) {
@@ -230,7 +252,7 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
             const uint32_t par = (uint32_t)((j / NS) & 1);
             unsigned char *slot = slot0 + (size_t)s * a.slot_bytes;
             if (a.use_tma) {
-                if (!warp_wait(full + s, par)) {
+                if (!slot_wait(full + s, par)) {
                     if (lane == 0) set_status_bit(a, DAQ_DEV_TIMEOUT);
                     break;
                 }
@@ -240,7 +262,7 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
                 plain_tile_load(a, tinfo[s], slot, tid, kSumThreads);
                 asm volatile("bar.sync 1, %0;" ::"r"(kSumThreads) : "memory");
             }
-            if (j >= NS && !warp_wait(mdone + s, par ^ 1u)) {
+            if (j >= NS && !slot_wait(mdone + s, par ^ 1u)) {
                 if (lane == 0) set_status_bit(a, DAQ_DEV_TIMEOUT);
                 break;
             }
@@ -268,6 +290,11 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
                 }
             }
         }
+        // a warp that stopped early leaves loads in flight: they land before
+        // the CTA may exit (a slot's latest phase; immediate when consumed)
+        if (tid == 0)
+            for (int k = 0; k < NS; ++k)
+                if (pend & (1u << k)) mbar_wait_bounded(full + k, (pend_par >> k) & 1u, kWaitLimitNs);
     } else if (warp < NSW + NS) {
         // ------------------------------------------------------------ marks, aggregate, Q bins of buffer s
         const int s = warp - NSW;
@@ -275,7 +302,7 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
         for (long long j = s;; j += NS) {
             const long long tile = first + j * G;
             if (tile >= total) break;
-            if (!warp_wait(sums + s, (uint32_t)((j / NS) & 1))) {
+            if (!slot_wait(sums + s, (uint32_t)((j / NS) & 1))) {
                 if (lane == 0) set_status_bit(a, DAQ_DEV_TIMEOUT);
                 break;
             }
@@ -682,12 +709,16 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
 
     uint32_t phase_bit = 0;
     bool store_pending = false;
+    bool load_pending = false;  // thread 32: a load issued whose phase no thread has waited for
     uint32_t nMt = 0, nfl2 = 0;
     TileRec nr{0, 0, 0, 0};
     TileExcl ne{0, 0, 0};
     int in_ok = 1;
     if (first < total) {
-        if (tid == 32) start_load(first, boxes_of(flags_of(first)));
+        if (tid == 32) {
+            start_load(first, boxes_of(flags_of(first)));
+            load_pending = true;
+        }
         if (warp == 0) in_ok = load_inputs(first, nMt, nr, ne, nfl2) ? 1 : 0;
     }
     for (long long tile = first; tile < total; tile += G) {
@@ -715,6 +746,7 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
         }
         if (a.use_tma) {
             const bool ok = mbar_wait_bounded(bar, phase_bit, kWaitLimitNs);
+            if (ok) load_pending = false;
             phase_bit ^= 1u;
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) set_status_bit(a, DAQ_DEV_TIMEOUT);
@@ -735,12 +767,20 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
         if (kFused && tid == 0) atomicAdd(compacted_ctr(a), 1ull);
         const long long next = tile + G;
         if (next < total) {
-            if (tid == 32) start_load(next, *s_boxes);
+            if (tid == 32) {
+                start_load(next, *s_boxes);
+                load_pending = a.use_tma;
+            }
             if (warp == 0) in_ok = load_inputs(next, nMt, nr, ne, nfl2) ? 1 : 0;
         }
         if (tid == 0) trace_stamp(a, tile, 7);
         // rows [ex.m, ex.m + agg.m) <- stage bytes [phase, phase + agg.m * 2X)
         long long ge = gs + agg.m * rb;
+        if ((a.flags & DAQ_DEBUG_CHECKS) && (ex.m < 0 || agg.m < 0 || agg.m > nt)) {
+            // the stage holds at most the tile's samples
+            if (tid == 0) set_status_bit(a, DAQ_DEV_BAD_INDEX);
+            ge = gs;
+        }
         const long long cap_b = a.pool_cap * rb;
         if (ge > cap_b) {
             ge = cap_b;
@@ -774,12 +814,14 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
         if (tid == 0) trace_stamp(a, tile, 9);
     }
     if (tid == 0 && store_pending) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    if (tid == 32 && load_pending) mbar_wait_bounded(bar, phase_bit, kWaitLimitNs);  // left early: let it land
 }
 
 template <int TW>
 __global__ void __launch_bounds__(256, 2) daq_compact_kernel(const __grid_constant__ KArgs a)
 {
-    pdl_wait();  // every tile's prefix
+    pdl_wait();                // every tile's prefix
+    if (aborted(a)) return;    // the scan gave up: its prefixes are incomplete
     extern __shared__ __align__(128) unsigned char smem[];
     compact_role<TW, false>(a, smem, blockIdx.x, gridDim.x);
 }
@@ -814,7 +856,7 @@ __device__ __forceinline__ void scan_role(const KArgs &a)
             for (uint32_t i = 0; !((hi >> 32) & (unsigned long long)kRecValid); ++i) {
                 __nanosleep(128);
                 ld_acquire_b128(recs + t, lo, hi);
-                if ((i & 63u) == 63u && (aborted(a) || global_ns() - t0 > kWaitLimitNs)) {
+                if (global_ns() - t0 > a.wait_ns || ((i & 63u) == 63u && aborted(a))) {
                     s_fail = 1;
                     break;
                 }

@@ -1,7 +1,7 @@
 """Multi-GPU form: independent replicas, one process per GPU.
 
 Every calorimeter-fill is processed independently (the experiment gives each
-calorimeter its own GPU, Sec. 2), so ranks share no data: each takes its own
+calorimeter its own GPU, Sec. 3), so ranks share no data: each takes its own
 share of the fills and keeps its own Q rows.  The only cross-rank step is the
 timing: a barrier before and after the timed region and the maximum of the
 ranks' elapsed times, from which the whole-job throughput is the units all

@@ -38,10 +38,49 @@ def test_every_declared_symbol_is_exported(daq):
 
 
 def test_struct_layouts_match_header(daq):
-    # daq_params: 8 int32, pointer, uint32 + 3 int32, 2 pointers, size_t, 2 pointers, 2 int32
-    assert ctypes.sizeof(daq.DaqParams) == 32 + 8 + 16 + 8 + 8 + 8 + 8 + 8 + 8
+    # daq_params: 8 int32, pointer, uint32 + 3 int32, 2 pointers, size_t, 2 pointers, 2 int32, uint64
+    assert ctypes.sizeof(daq.DaqParams) == 32 + 8 + 16 + 8 + 8 + 8 + 8 + 8 + 8 + 8
     assert ctypes.sizeof(daq.DaqIslands) == 6 * 8
     assert daq.ISLAND_DTYPE.itemsize == 24
+
+
+def test_binding_layout_matches_the_c_compiler(daq, tmp_path):
+    """The ctypes mirror of daq_params and daq_islands has the sizes and field
+    offsets a C compiler gives the header's structs."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "daq.h"\n'
+        'int main(void) { printf("%zu %zu %zu %zu %zu\\n", sizeof(daq_params), offsetof(daq_params, wait_limit_ns),'
+        ' offsetof(daq_params, lag_tiles), offsetof(daq_params, stream), sizeof(daq_islands)); return 0; }\n')
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    P = daq.DaqParams
+    assert got == [ctypes.sizeof(P), P.wait_limit_ns.offset, P.lag_tiles.offset, P.stream.offset,
+                   ctypes.sizeof(daq.DaqIslands)]
+
+
+def test_debug_checks_flag_and_status(daq):
+    """DAQ_DEBUG_CHECKS is its own flag bit; a failed device index check
+    (DAQ_DEV_BAD_INDEX) maps to DAQ_EINDEX, after timeouts and bad fill
+    lengths and before capacity shortfalls."""
+    flags = [daq.DAQ_SKIP_Q, daq.DAQ_SKIP_ISLANDS, daq.DAQ_SYNC, daq.DAQ_PACK_POOL, daq.DAQ_DEBUG_CHECKS]
+    assert len(set(flags)) == len(flags) and all(f & (f - 1) == 0 for f in flags)
+    bits = [daq.DAQ_DEV_HDR_OVERFLOW, daq.DAQ_DEV_POOL_OVERFLOW, daq.DAQ_DEV_TIMEOUT, daq.DAQ_DEV_BAD_FILL_LEN,
+            daq.DAQ_DEV_BAD_INDEX]
+    assert len(set(bits)) == len(bits) and all(b & (b - 1) == 0 for b in bits)
+    assert daq.daq_status_from_counts([0, 0, daq.DAQ_DEV_BAD_INDEX, 0]) == daq.DAQ_EINDEX
+    assert daq.daq_status_from_counts([0, 0, daq.DAQ_DEV_BAD_INDEX | daq.DAQ_DEV_POOL_OVERFLOW, 0]) == daq.DAQ_EINDEX
+    assert daq.daq_status_from_counts([0, 0, daq.DAQ_DEV_BAD_INDEX | daq.DAQ_DEV_TIMEOUT, 0]) == daq.DAQ_ETIMEOUT
+    assert "index" in daq.strerror(daq.DAQ_EINDEX)
+    assert daq.make_params(flags=daq.DAQ_DEBUG_CHECKS).flags == daq.DAQ_DEBUG_CHECKS
+    assert daq.make_params(wait_limit_ns=1000).wait_limit_ns == 1000
+    assert daq.lib().daq_version() >= 102
 
 
 def test_host_calls(daq):

@@ -197,3 +197,72 @@ def test_sparse_regime(env, grid):
     s = env["synth"].generate(w.config())
     res, ref = compare(env, s, w.params(), grid=grid)
     assert 0.02 < ref["n_rows"] / (3 * s.shape[3]) < 0.2
+
+
+def test_debug_checks_change_nothing_on_the_full_fill(env):
+    """DAQ_DEBUG_CHECKS: the benchmark fill gives the same records, rows,
+    pedestals and Q with the checks on as with them off, and no check fails."""
+    torch, daq = env["torch"], env["daq"]
+    from synth import workloads as W
+    w = W.PLAIN_FULL_FILL
+    s = torch.from_numpy(env["synth"].generate(w.config(), n_threads=16)).cuda()
+    plain = daq.process_fills(s, **w.params())
+    checked = daq.process_fills(s, flags=daq.DAQ_DEBUG_CHECKS, **w.params())
+    assert plain["status"] == checked["status"] == daq.DAQ_OK
+    assert checked["counts"][2] == 0
+    assert plain["n_islands"] == checked["n_islands"] and plain["n_rows"] == checked["n_rows"]
+    n, r = plain["n_rows"], plain["n_islands"]
+    assert torch.equal(plain["outputs"].hdr[: 3 * r], checked["outputs"].hdr[: 3 * r])
+    assert torch.equal(plain["outputs"].pool[:n], checked["outputs"].pool[:n])
+    assert torch.equal(plain["outputs"].pedestal, checked["outputs"].pedestal)
+    assert torch.equal(plain["q"], checked["q"])
+
+
+@pytest.mark.parametrize("seed", range(0, 40, 3))
+def test_random_shapes_with_debug_checks(env, seed):
+    """The random cases again with every index checked before its store:
+    bit-exact against the oracle and no check fails."""
+    rng = np.random.default_rng(1000 + seed)
+    s, params, fill_len, tile = _random_case(rng)
+    grid = int(rng.choice([0, -1, -4, -5, -6]))
+    res, _ = compare(env, s, params, fill_len=fill_len, tile=tile, grid=grid, flags=env["daq"].DAQ_DEBUG_CHECKS)
+    assert res["counts"][2] == 0
+
+
+@pytest.mark.parametrize("grid", [0, -1, -2, -3, -4, -5, -6])
+def test_short_wait_limit_gives_up_cleanly(env, grid):
+    """A 1 us limit on the waits for other CTAs' published state: the call ends
+    (every CTA stops and its copies land), returns DAQ_OK or DAQ_ETIMEOUT, and
+    the next call with the default limit is bit-exact against the oracle."""
+    torch, daq, oracle = env["torch"], env["daq"], env["oracle"]
+    from synth import workloads as W
+    w = W.scaled(W.PLAIN_FULL_FILL, n_calo=4, n_samples=120_000)
+    s = env["synth"].generate(w.config())
+    ds = torch.from_numpy(s).cuda()
+    statuses = []
+    for _ in range(3):
+        r = daq.process_fills(ds, grid=grid, wait_limit_ns=1000, allow=(daq.DAQ_ETIMEOUT,), **w.params())
+        torch.cuda.synchronize()
+        assert r["status"] in (daq.DAQ_OK, daq.DAQ_ETIMEOUT), r["status"]
+        assert r["status"] == daq.DAQ_OK or r["counts"][2] & daq.DAQ_DEV_TIMEOUT
+        statuses.append(r["status"])
+    compare(env, s, w.params(), grid=grid)
+
+
+def test_wait_limit_runs_out_and_the_next_call_is_exact(env):
+    """The plain single-pass form launches one CTA per tile, and a tile's
+    look-back reads the states its predecessors publish as they finish: on a
+    fill of some 5,000 tiles many find one not yet published and must wait.
+    With a 1 ns limit (the clock is read on every poll) such a wait runs out at
+    its first poll.  The call returns DAQ_ETIMEOUT (flag set, no hang: every CTA
+    returned), and the next call is bit-exact."""
+    torch, daq = env["torch"], env["daq"]
+    from synth import workloads as W
+    w = W.scaled(W.PLAIN_FULL_FILL, n_calo=4)
+    s = env["synth"].generate(w.config())
+    ds = torch.from_numpy(s).cuda()
+    r = daq.process_fills(ds, grid=-1, wait_limit_ns=1, allow=(daq.DAQ_ETIMEOUT,), **w.params())
+    torch.cuda.synchronize()
+    assert r["status"] == daq.DAQ_ETIMEOUT and r["counts"][2] & daq.DAQ_DEV_TIMEOUT
+    compare(env, s, w.params(), grid=-1)
+    compare(env, s, w.params(), grid=0)

@@ -42,8 +42,12 @@ def test_static_scratch_matches_regular_call_twice(env):
         out = _outputs(torch, daq, F, C, X, F * C * N)
         q = torch.zeros(daq.q_size(C, N, params["decim"]), dtype=torch.int64, device="cuda")
         p = daq.make_params(**params, flags=daq.DAQ_SYNC, stream=torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         rc = daq.daq_process_fills_static(s.data_ptr(), C, X, N, F, p, out.struct(), q.data_ptr())
         assert rc == daq.DAQ_OK, (call, rc, daq.strerror(rc))
+        if call == 1:  # the first call may place the area (lazy module loading); the second allocates nothing
+            assert torch.cuda.mem_get_info()[0] == free_before
         counts = out.counts.cpu().numpy()
         assert int(counts[0]) == n_isl and int(counts[1]) == n_rows, call
         assert np.array_equal(out.islands_host(n_isl), ref_out.islands_host(n_isl)), call
