@@ -1041,41 +1041,53 @@ static cudaError_t launch_pdl(K kernel, int grid, int block, size_t smem, cudaSt
     return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
+// The count kernel for NS slots, halo-free or not, grids from occupancy when
+// grid <= 0.
+template <int TW, int NS, bool HF>
+static cudaError_t launch_count(const KArgs &a, const Plan &pl, int grid, int sms, int64_t tiles, cudaStream_t s)
+{
+    static size_t conf[64] = {0};
+    cudaError_t e = ensure_smem(daq_count_kernel<TW, NS, HF>, pl.smem, conf);
+    if (e != cudaSuccess) return e;
+    if (grid <= 0) {
+        int per = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, daq_count_kernel<TW, NS, HF>, count_threads<NS>(), pl.smem);
+        if (e != cudaSuccess) return e;
+        if (per < 1) return cudaErrorInvalidConfiguration;
+        grid = per * sms;
+    }
+    grid = (int)std::min<int64_t>(grid, tiles);
+    return launch_pdl(daq_count_kernel<TW, NS, HF>, grid, count_threads<NS>(), pl.smem, s, a);
+}
+
 // Count pass, scan, compact pass.  Events (optional): [2] after the count
 // kernel, [3] after the scan, [4] after the compact kernel.
 template <int TW>
 static cudaError_t launch_twopass(const KArgs &a, const Plan &pl, int grid, int sms, bool skip_isl,
                                   cudaEvent_t const *ev, cudaStream_t s)
 {
-    static size_t conf_a[64] = {0}, conf_a3[64] = {0}, conf_b[64] = {0};
-    const bool ns3 = pl.count_ns == 3;
-    const int count_thr = ns3 ? count_threads<3>() : count_threads<2>();
-    cudaError_t e = ns3 ? ensure_smem(daq_count_kernel<TW, 3>, pl.smem, conf_a3)
-                        : ensure_smem(daq_count_kernel<TW, 2>, pl.smem, conf_a);
-    if (e != cudaSuccess) return e;
-    e = ensure_smem(daq_compact_kernel<TW>, pl.smem_b, conf_b);
+    static size_t conf_b[64] = {0};
+    cudaError_t e = ensure_smem(daq_compact_kernel<TW>, pl.smem_b, conf_b);
     if (e != cudaSuccess) return e;
     const int64_t tiles = std::max<int64_t>(1, pl.max_tiles);
-    int grid_a = grid, grid_b = grid;
+    int grid_b = grid;
     if (grid <= 0) {
-        int per_a = 0, per_b = 0;
-        e = ns3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_a, daq_count_kernel<TW, 3>, count_thr, pl.smem)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_a, daq_count_kernel<TW, 2>, count_thr, pl.smem);
-        if (e != cudaSuccess) return e;
+        int per_b = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_b, daq_compact_kernel<TW>, 256, pl.smem_b);
         if (e != cudaSuccess) return e;
-        if (per_a < 1 || per_b < 1) return cudaErrorInvalidConfiguration;
-        grid_a = per_a * sms;
+        if (per_b < 1) return cudaErrorInvalidConfiguration;
         grid_b = per_b * sms;
     }
-    grid_a = (int)std::min<int64_t>(grid_a, tiles);
     grid_b = (int)std::min<int64_t>(grid_b, tiles);
-    e = ns3 ? launch_pdl(daq_count_kernel<TW, 3>, grid_a, count_thr, pl.smem, s, a)
-            : launch_pdl(daq_count_kernel<TW, 2>, grid_a, count_thr, pl.smem, s, a);
+    e = pl.halo_free             ? launch_count<TW, 2, true>(a, pl, grid, sms, tiles, s)
+        : pl.count_ns == 3       ? launch_count<TW, 3, false>(a, pl, grid, sms, tiles, s)
+                                 : launch_count<TW, 2, false>(a, pl, grid, sms, tiles, s);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
     const int scan_blocks = (int)((tiles + kScanChunk - 1) / kScanChunk);
-    if ((e = launch_pdl(daq_scan_kernel<TW>, scan_blocks, kScanThreads, 0, s, a)) != cudaSuccess) return e;
+    e = pl.halo_free ? launch_pdl(daq_scan_kernel<TW, true>, scan_blocks, kScanThreads, 0, s, a)
+                     : launch_pdl(daq_scan_kernel<TW, false>, scan_blocks, kScanThreads, 0, s, a);
+    if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
     if (!skip_isl && (e = launch_pdl(daq_compact_kernel<TW>, grid_b, 256, pl.smem_b, s, a)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[4], s)) != cudaSuccess) return e;

@@ -183,7 +183,8 @@ __device__ __forceinline__ bool wait_counter_ge(const KArgs &a, const unsigned l
 // kFused: a tile is loaded only while it is at most lag_tiles ahead of the
 // tiles compacted, and its aggregate is published with a release store and a
 // valid bit for the scanner.
-template <int TW, bool kFused, int NS = 2>
+// kHaloFree: the count pass loads the tile proper only (see complete_tile).
+template <int TW, bool kFused, int NS = 2, bool kHaloFree = false>
 __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, long long first, long long G)
 {
     constexpr int NWT = TW / 32, NBT = TW / 8;
@@ -232,8 +233,10 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(full + s, tile_load_bytes(a));
             issue_tile_load(a, T, slot0 + (size_t)s * a.slot_bytes, full + s);
-            pend |= 1u << s;
-            pend_par = (pend_par & ~(1u << s)) | ((uint32_t)(((tile - first) / G / NS) & 1) << s);
+            if (kFused) {  // the single-launch form may stop early: loads in flight are waited for at exit
+                pend |= 1u << s;
+                pend_par = (pend_par & ~(1u << s)) | ((uint32_t)(((tile - first) / G / NS) & 1) << s);
+            }
         }
         trace_stamp(a, tile, 1);
     };
@@ -292,7 +295,7 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
         }
         // a warp that stopped early leaves loads in flight: they land before
         // the CTA may exit (a slot's latest phase; immediate when consumed)
-        if (tid == 0)
+        if (kFused && tid == 0)
             for (int k = 0; k < NS; ++k)
                 if (pend & (1u << k)) mbar_wait_bounded(full + k, (pend_par >> k) & 1u, kWaitLimitNs);
     } else if (warp < NSW + NS) {
@@ -307,7 +310,7 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
                 break;
             }
             const TileInfo T = tinfo_m[s];
-            if (!kFused && a.halo_free) {
+            if (kHaloFree) {
                 // internal marks of the tile and its first / last crossing; the
                 // scan adds the marks that crossings of neighbouring tiles reach
                 const uint32_t A = lane < NWT ? reinterpret_cast<const uint32_t *>(abyte0 + 128 * s)[lane] : 0u;
@@ -361,14 +364,14 @@ __device__ __forceinline__ void count_role(const KArgs &a, unsigned char *smem, 
 }
 
 // NS = 2: two CTAs per SM; NS = 3: one CTA per SM with 16 sum warps, for
-// extended tiles too wide for two CTAs' slots to fit.
-template <int TW, int NS>
+// extended tiles too wide for two CTAs' slots to fit.  HF: halo-free.
+template <int TW, int NS, bool HF>
 __global__ void __launch_bounds__(count_threads<NS>(), NS == 2 ? 2 : 1) daq_count_kernel(const __grid_constant__ KArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     pdl_wait();     // the prepare kernel's plan, pedestals and resets
     pdl_trigger();  // the scan may be scheduled as CTAs finish
-    count_role<TW, false, NS>(a, smem, blockIdx.x, gridDim.x);
+    count_role<TW, false, NS, HF>(a, smem, blockIdx.x, gridDim.x);
 }
 
 // ============================================================================ scan of the aggregates
@@ -485,9 +488,9 @@ template <int TW> __device__ TileRec complete_tile(const KArgs &a, long long j)
 // order (so every chunk's predecessors are running or done); each reduces its chunk,
 // publishes the aggregate, looks back over earlier chunks' published states
 // for its exclusive prefix (one warp), publishes its inclusive prefix and
-// writes every tile's exclusive prefix.  After a halo-free count pass it first
-// completes its tiles' marks and records.
-template <int TW>
+// writes every tile's exclusive prefix.  After a halo-free count pass (HF) it
+// first completes its tiles' marks and records.
+template <int TW, bool HF>
 __global__ void __launch_bounds__(kScanThreads) daq_scan_kernel(const __grid_constant__ KArgs a)
 {
     pdl_wait();  // every tile's record
@@ -509,7 +512,7 @@ __global__ void __launch_bounds__(kScanThreads) daq_scan_kernel(const __grid_con
 #pragma unroll
     for (int i = 0; i < kScanPer; ++i) {
         if (base + i >= total) r[i] = TileRec{0, 0, 0, 1};
-        else if (a.halo_free) {
+        else if (HF) {
             r[i] = complete_tile<TW>(a, base + i);
             recs[base + i] = r[i];  // the compact pass reads the completed record and marks
         } else r[i] = recs[base + i];
@@ -709,7 +712,7 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
 
     uint32_t phase_bit = 0;
     bool store_pending = false;
-    bool load_pending = false;  // thread 32: a load issued whose phase no thread has waited for
+    bool load_pending = false;  // thread 32 (single-launch form): a load issued that no thread has waited for
     uint32_t nMt = 0, nfl2 = 0;
     TileRec nr{0, 0, 0, 0};
     TileExcl ne{0, 0, 0};
@@ -717,7 +720,7 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
     if (first < total) {
         if (tid == 32) {
             start_load(first, boxes_of(flags_of(first)));
-            load_pending = true;
+            load_pending = kFused;
         }
         if (warp == 0) in_ok = load_inputs(first, nMt, nr, ne, nfl2) ? 1 : 0;
     }
@@ -769,7 +772,7 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
         if (next < total) {
             if (tid == 32) {
                 start_load(next, *s_boxes);
-                load_pending = a.use_tma;
+                load_pending = kFused && a.use_tma;  // the single-launch form may stop before waiting for it
             }
             if (warp == 0) in_ok = load_inputs(next, nMt, nr, ne, nfl2) ? 1 : 0;
         }
