@@ -700,14 +700,14 @@ def bench_stress(args, torch, dev, daq, synth, W) -> dict:
     one call over all 48 fills; the fills cycle over 4 distinct generated
     fills (the kernels cannot tell)."""
     import numpy as np
-    w = W.STRESS
+    w = W.STRESS if args.stress_fills == W.STRESS.n_fills else W.scaled(W.STRESS, n_fills=args.stress_fills)
     params = w.params()
     F, C, X, N = w.n_fills, w.n_calo, 54, w.n_samples
     free, _ = torch.cuda.mem_get_info(dev)
     need = 2 * F * C * X * N * 2 + (8 << 30)
     if free < need:
         return {"skipped": f"needs {need / 1e9:.0f} GB free device memory, {free / 1e9:.0f} GB free"}
-    n_distinct = 4
+    n_distinct = min(4, F)
     t0 = time.perf_counter()
     x = torch.empty((F, C, X, N), dtype=torch.int16, device=dev)
     stage = torch.empty((1, C, X, N), dtype=torch.int16).pin_memory()
@@ -726,7 +726,7 @@ def bench_stress(args, torch, dev, daq, synth, W) -> dict:
     res = {"value": round(Ks * raw / (total * 1e-3) / 1e9, 2), "unit": UNIT, "steps": Ks,
            "ms_per_batch": round(total / Ks, 3), "latency_ms_p99": round(float(np.percentile(ms, 99)), 3),
            "pct_of_hbm_peak": round(100.0 * Ks * raw / (total * 1e-3) / 1e9 / measured_peaks()[0], 2),
-           "workload": "48 fills x 24 calorimeters x 54 crystals x 560,000 int16 (69.67 GB device-resident), "
+           "workload": f"{F} fills x 24 calorimeters x 54 crystals x 560,000 int16 ({raw / 1e9:.2f} GB device-resident), "
                        "10x pulse rate (~15,000 pulses per calorimeter-fill), T=15, pre=8, post=64, D=8 and 32; "
                        "fills cycle over 4 distinct generated fills",
            "raw_bytes_per_batch": raw, "islands_per_batch": int(counts[0]), "pool_rows_per_batch": int(counts[1]),
@@ -1064,6 +1064,7 @@ def main():
     ap.add_argument("--no-served", action="store_true", help="skip the served (request loop) form")
     ap.add_argument("--no-stress", action="store_true", help="skip the 48-fill (69.67 GB) stress batch")
     ap.add_argument("--stress-steps", type=int, default=10)
+    ap.add_argument("--stress-fills", type=int, default=48, help="fills of the stress batch (48; fewer for profiling)")
     ap.add_argument("--no-sparse", action="store_true", help="skip the sparse-regime fill")
     ap.add_argument("--no-threshold-scan", action="store_true", help="skip the island-efficiency threshold scan")
     ap.add_argument("--no-crystal-sum", action="store_true", help="skip the per-crystal full-resolution fill sum")
