@@ -22,14 +22,15 @@
 //                (row 1), threshold bits (row 2), 8-sample block sums, and the
 //                raw rows of the samples into a park slot of Tensor Memory;
 //   marks warps  pre/post windows and merge (rows 3-4), the tile aggregate
-//                (published for the look-back), the rank table (pool row of
-//                each marked sample within the tile, -1 if unmarked), Q
-//                partial bins (rows 7-8); two warps take alternate tiles;
+//                (published for the look-back), Q partial bins (rows 7-8);
+//                two warps take alternate tiles;
 //   look-back    decoupled look-back over earlier tiles' published states
 //                (four warps, tiles in turn): the tile's exclusive prefix;
-//   stage warps  (one per Tensor Memory lane quadrant) once the prefix is
-//                known, read the rows back and store the marked ones at
-//                phase + rank * 2 n_xtal bytes of an out-stage (row 5);
+//   stage warps  (two per Tensor Memory lane quadrant, taking its steps in
+//                turn) once the prefix is known, read the rows back and store
+//                the marked ones at phase + rank * 2 n_xtal bytes of an
+//                out-stage, rank = the sample's pool row within the tile from
+//                the marks words (row 5);
 //   bulk warp    one bulk copy of the out-stage to the pool (plus unaligned
 //                ends);
 //   record warp  the tile's island records and, after the last tile, the
@@ -67,7 +68,8 @@ constexpr int kPkLook = kPkMarks + kPkNMarks;
 constexpr int kPkNLook = 4;
 constexpr int kPkRec = kPkLook + kPkNLook;
 constexpr int kPkStage0 = kPkRec + 1;
-constexpr int kPkBulk = kPkStage0 + 4;
+constexpr int kPkNStage = 8;  // two per Tensor Memory quadrant
+constexpr int kPkBulk = kPkStage0 + kPkNStage;
 constexpr int kPkWarps = kPkBulk + 1;
 constexpr int kPkThreads = 32 * kPkWarps;
 constexpr int kPkNCSlot = 2;     // count slots (extended tile)
@@ -85,7 +87,6 @@ template <int TW> struct ParkMeta {
     int32_t blocksum[TW / 8];
     uint32_t wm[TW / 32], ws[TW / 32], we[TW / 32];
     int32_t wmb[TW / 32], wsb[TW / 32], wls[TW / 32];
-    int16_t rank[TW];  // pool row of sample t0 + t within the tile, -1 if unmarked
 };
 
 template <int TW> __host__ __device__ constexpr size_t park_meta_bytes() { return (sizeof(ParkMeta<TW>) + 15) & ~size_t(15); }
@@ -120,8 +121,8 @@ struct ParkBars {
     __host__ __device__ int count() const { return 4 * nm + 2 * kPkNCSlot + 2 * no + 2 * np; }
 };
 // arrivals that free a tile record: the marks warp (after its Q bins), the
-// four stage warps, the bulk warp and the record warp
-constexpr int kPkMetaFreeArrivals = 7;
+// stage warps, the bulk warp and the record warp
+constexpr int kPkMetaFreeArrivals = 1 + kPkNStage + 1 + 1;
 
 // Shared-memory layout: count slots, out-stages, tile records, sample sums
 // (decimation factors that are not multiples of 8), barriers, fill plan, end
@@ -171,37 +172,9 @@ __device__ __forceinline__ int park_wait(const KArgs &a, uint64_t *bar, uint32_t
     return __shfl_sync(kFull, r, 0);
 }
 
-__device__ __forceinline__ int lds_s16(uint32_t addr)
-{
-    int16_t v;
-    asm volatile("ld.shared.s16 %0, [%1];" : "=h"(v) : "r"(addr) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ void sts_u32(uint32_t addr, uint32_t v)
 {
     asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-
-// Rank table of a tile (one warp; lane w holds marks word w of the tile and mb
-// = marked samples before the word): rank[t] = pool row of sample t0 + t within
-// the tile, -1 for unmarked samples.  Two samples per 32-bit store.
-template <int TW>
-__device__ __forceinline__ void rank_table(uint32_t Mt, int mb, int16_t *rank, int lane)
-{
-    constexpr int NWT = TW / 32;
-    if (lane >= NWT) return;
-    uint32_t *out = reinterpret_cast<uint32_t *>(rank + 32 * lane);
-    int r = mb;
-#pragma unroll
-    for (int b = 0; b < 32; b += 2) {
-        const int m0 = (Mt >> b) & 1, m1 = (Mt >> (b + 1)) & 1;
-        const int v0 = m0 ? r : -1;
-        r += m0;
-        const int v1 = m1 ? r : -1;
-        r += m1;
-        out[b >> 1] = (uint32_t)(uint16_t)v0 | ((uint32_t)(uint16_t)v1 << 16);
-    }
 }
 
 // One warp step of the crystal sum (as sum_pass_step: lane L owns extended
@@ -313,12 +286,12 @@ __global__ void __launch_bounds__(kPkThreads, 1) daq_park_kernel(const __grid_co
             mbar_init(bar(BI.cempty(s)), kPkNSum);
         }
         for (int o = 0; o < NO; ++o) {
-            mbar_init(bar(BI.ofull(o)), 4);
+            mbar_init(bar(BI.ofull(o)), kPkNStage);
             mbar_init(bar(BI.ofree(o)), 1);
         }
         for (int p = 0; p < NP; ++p) {
             mbar_init(bar(BI.pfull(p)), kPkNSum);
-            mbar_init(bar(BI.pfree(p)), 4);
+            mbar_init(bar(BI.pfree(p)), kPkNStage);
         }
         fence_mbar_init();
     }
@@ -419,11 +392,6 @@ __global__ void __launch_bounds__(kPkThreads, 1) daq_park_kernel(const __grid_co
                 M->agg = agg;
                 if (T.tile > 0) publish(a.status, T.tile, false, agg, true);
             }
-            if (!skip_isl) {
-                __syncwarp();
-                const int wl = lane < TW / 32 ? lane : 0;
-                rank_table<TW>(M->wm[wl], M->wmb[wl], M->rank, lane);
-            }
             __syncwarp();
             if (lane == 0) {
                 trace_stamp(a, T.tile, 4);
@@ -473,9 +441,10 @@ __global__ void __launch_bounds__(kPkThreads, 1) daq_park_kernel(const __grid_co
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(BI.meta_free(m)));
         }
-    } else if (warp >= kPkStage0 && warp < kPkStage0 + 4) {
+    } else if (warp >= kPkStage0 && warp < kPkStage0 + kPkNStage) {
         // ------------------------------------------------------------ Tensor Memory -> out-stage (marked rows)
-        const int q = warp - kPkStage0;
+        // Warps q and q + 4 share quadrant q and take its steps in turn.
+        const int q = (warp - kPkStage0) & 3, half = (warp - kPkStage0) >> 2;
         const uint32_t tq = tbase + ((uint32_t)(32 * q) << 16);
         for (long long i = 0;; ++i) {
             const int m = (int)(i % NM), p = (int)(i % NP), o = (int)(i % NO);
@@ -497,12 +466,21 @@ __global__ void __launch_bounds__(kPkThreads, 1) daq_park_kernel(const __grid_co
             if (rows) {
                 const int nt = (int)(T.t_end - T.t0);
                 const uint32_t out_s = smem_addr(out0 + (size_t)o * out_bytes) + (uint32_t)((excl.m * rb) & 15);
-                const uint32_t rank_s = smem_addr(M->rank);
+                // pool row within the tile of tile column c, -1 if unmarked (c, c + 1 share a marks word)
+                const int ca0 = 2 * lane - a.hl;
+                int nq = 0;  // steps of this quadrant so far
                 for (int it = 0; it < n_steps; ++it) {
                     if (((kPkSum0 + it % kPkNSum) & 3) != q) continue;  // another quadrant's step
-                    const int ca = 64 * it + 2 * lane - a.hl;          // tile column of the lane's first sample
-                    const int ra = ca >= 0 && ca < nt ? lds_s16(rank_s + 2u * (uint32_t)ca) : -1;
-                    const int rbk = ca + 1 >= 0 && ca + 1 < nt ? lds_s16(rank_s + 2u * (uint32_t)(ca + 1)) : -1;
+                    if ((nq++ & 1) != half) continue;                    // the other warp of the quadrant's
+                    const int ca = 64 * it + ca0;                        // tile column of the lane's first sample
+                    int ra = -1, rbk = -1;
+                    if (ca >= 0 && ca < nt) {
+                        const int w = ca >> 5, b = ca & 31;  // b even: ca + 1 is in the same word
+                        const uint32_t mw = M->wm[w];
+                        const int before = M->wmb[w] + __popc(mw & ((1u << b) - 1u));
+                        if ((mw >> b) & 1u) ra = before;
+                        if (ca + 1 < nt && ((mw >> (b + 1)) & 1u)) rbk = before + (int)((mw >> b) & 1u);
+                    }
                     const uint32_t tcol = tq + (uint32_t)(p * PC + park_step_col(it, cps));
                     for (int x0 = 0; x0 < X; x0 += 16) {
                         uint32_t v[16];
