@@ -21,7 +21,7 @@ LIB_PATH = _build.LIB
 DAQ_OK, DAQ_EINVAL, DAQ_ECAPACITY, DAQ_ECUDA, DAQ_ETIMEOUT, DAQ_EUNSUPPORTED, DAQ_ESCRATCH, DAQ_EINDEX = \
     0, -1, -2, -3, -4, -5, -6, -7
 DAQ_STATIC_SCRATCH_BYTES = 8 << 20
-DAQ_SKIP_Q, DAQ_SKIP_ISLANDS, DAQ_SYNC, DAQ_PACK_POOL, DAQ_DEBUG_CHECKS = 1, 2, 4, 8, 16
+DAQ_SKIP_Q, DAQ_SKIP_ISLANDS, DAQ_SYNC, DAQ_PACK_POOL, DAQ_DEBUG_CHECKS, DAQ_SPARSE = 1, 2, 4, 8, 16, 32
 DAQ_DEV_HDR_OVERFLOW, DAQ_DEV_POOL_OVERFLOW, DAQ_DEV_TIMEOUT, DAQ_DEV_BAD_FILL_LEN, DAQ_DEV_BAD_INDEX = 1, 2, 4, 8, 16
 
 ISLAND_DTYPE = np.dtype([("fill", "<i4"), ("calo", "<i4"), ("start", "<i4"), ("len", "<i4"),
@@ -53,7 +53,8 @@ class DaqHostIO(ctypes.Structure):
 
 class DaqTuneResult(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("grid", ctypes.c_int32), ("n_tried", ctypes.c_int32),
-                ("from_cache", ctypes.c_int32), ("ms", ctypes.c_float), ("ms_default", ctypes.c_float)]
+                ("from_cache", ctypes.c_int32), ("ms", ctypes.c_float), ("ms_default", ctypes.c_float),
+                ("flags", ctypes.c_uint32)]
 
 
 DAQ_TUNE, DAQ_TUNE_FORCE = 1, 2
@@ -504,7 +505,7 @@ class BatchPlan:
     def tuning(self) -> dict:
         r = daq_batch_plan_tuning(self._h)
         return dict(tile=r.tile, grid=r.grid, n_tried=r.n_tried, from_cache=bool(r.from_cache), ms=r.ms,
-                    ms_default=r.ms_default)
+                    ms_default=r.ms_default, flags=r.flags)
 
     def close(self) -> None:
         if getattr(self, "_h", None):

@@ -39,7 +39,7 @@ namespace {
 using TuneKey = std::tuple<int, int, int, int64_t, int, int, int, int, int, int, int, int, uint32_t, int>;
 
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;  // key -> (tile, grid)
+std::map<TuneKey, std::tuple<int, int, uint32_t>> g_tune_cache;  // key -> (tile, grid, DAQ_SPARSE or 0)
 
 TuneKey tune_key(int dev, int C, int X, int64_t N, int F, const daq_params &p)
 {
@@ -50,16 +50,19 @@ TuneKey tune_key(int dev, int C, int X, int64_t N, int F, const daq_params &p)
 
 struct Candidate {
     int tile, grid;
+    uint32_t flags;  // DAQ_SPARSE or 0
 };
 
 // Form x tile x CTAs: the default (two-pass, tile chosen by the library), the
-// two-pass form at 128 / 224 / 384 / 448 with occupancy grids (2 CTAs per SM)
-// and with one CTA per SM, and the single-launch form at 448.  The single-pass
+// same with the compact pass that passes over tiles without marks (DAQ_SPARSE),
+// the two-pass form at 128 / 224 / 384 / 448 with occupancy grids (2 CTAs per
+// SM) and with one CTA per SM, and the single-launch form at 448.  The single-pass
 // forms (plain, persistent, pipelined, streaming, single-read) are not timed:
 // on every workload measured they were slower than the two-pass form.
 std::vector<Candidate> candidates(int sms)
 {
-    return {{0, 0}, {448, 0}, {384, 0}, {224, 0}, {128, 0}, {448, sms}, {224, sms}, {448, -4}};
+    return {{0, 0, 0u},   {0, 0, DAQ_SPARSE}, {448, 0, 0u},   {384, 0, 0u},
+            {224, 0, 0u}, {128, 0, 0u},       {448, sms, 0u}, {224, sms, 0u}, {448, -4, 0u}};
 }
 
 int q_values(int64_t N, int C, const daq_params &p, int64_t *n)
@@ -92,6 +95,7 @@ int run_once(const daq_batch_plan *pl, const daq_params &base, Candidate c, void
     daq_params p = base;
     p.tile = c.tile;
     p.grid = c.grid;
+    p.flags = (p.flags & ~DAQ_SPARSE) | c.flags;
     p.stream = s;
     p.workspace = ws;
     p.workspace_bytes = ws_bytes;
@@ -161,7 +165,7 @@ int daq_batch_plan_create(const int16_t *samples, int n_calo, int n_xtal, int64_
 
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device);
-    Candidate best{params->tile, params->grid};
+    Candidate best{params->tile, params->grid, params->flags & DAQ_SPARSE};
     pl->tune.tile = best.tile;
     pl->tune.grid = best.grid;
     const TuneKey key = tune_key(pl->device, n_calo, n_xtal, n_samples, n_fills, *params);
@@ -170,7 +174,7 @@ int daq_batch_plan_create(const int16_t *samples, int n_calo, int n_xtal, int64_
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            best = Candidate{it->second.first, it->second.second};
+            best = Candidate{std::get<0>(it->second), std::get<1>(it->second), std::get<2>(it->second)};
             cached = true;
         }
     }
@@ -187,6 +191,7 @@ int daq_batch_plan_create(const int16_t *samples, int n_calo, int n_xtal, int64_
             daq_params pc = pl->p;
             pc.tile = c.tile;
             pc.grid = c.grid;
+            pc.flags = (pc.flags & ~DAQ_SPARSE) | c.flags;
             size_t need = 0;
             if (daq_workspace_size(n_calo, n_xtal, n_samples, n_fills, &pc, &need) != DAQ_OK) continue;
             if (own) {
@@ -218,7 +223,7 @@ int daq_batch_plan_create(const int16_t *samples, int n_calo, int n_xtal, int64_
             cudaEventElapsedTime(&ms, e0, e1);
             ms /= kReps;
             ++tried;
-            if (c.tile == 0 && c.grid == 0) pl->tune.ms_default = ms;
+            if (c.tile == 0 && c.grid == 0 && c.flags == 0u) pl->tune.ms_default = ms;
             if (best_ms < 0.f || ms < best_ms) {
                 best_ms = ms;
                 best = c;
@@ -231,13 +236,15 @@ int daq_batch_plan_create(const int16_t *samples, int n_calo, int n_xtal, int64_
         pl->tune.n_tried = tried;
         pl->tune.ms = best_ms;
         std::lock_guard<std::mutex> g(g_tune_mu);
-        g_tune_cache[key] = {best.tile, best.grid};
+        g_tune_cache[key] = std::make_tuple(best.tile, best.grid, best.flags);
     }
     pl->tune.tile = best.tile;
     pl->tune.grid = best.grid;
+    pl->tune.flags = best.flags;
     pl->tune.from_cache = cached ? 1 : 0;
     pl->p.tile = best.tile;
     pl->p.grid = best.grid;
+    pl->p.flags = (pl->p.flags & ~DAQ_SPARSE) | best.flags;
 
     size_t need = 0;
     if ((rc = daq_workspace_size(n_calo, n_xtal, n_samples, n_fills, &pl->p, &need)) != DAQ_OK) return fail(rc);

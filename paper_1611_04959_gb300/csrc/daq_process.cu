@@ -750,7 +750,7 @@ static size_t count_smem_bytes(int tw, int slot_bytes, int need_sarr)
 static size_t compact_smem_bytes(int tw, int X, int slot_bytes_b)
 {
     size_t b = (size_t)slot_bytes_b + (size_t)(((tw * 2 * X + 32) + 15) & ~15) + (size_t)(tw / 32) * 4 * 6;
-    b += 16 + sizeof(TileInfo) + 2 * sizeof(Agg) + 8 + 8 * (kPlanSmem + 1) + 4 * kPlanSmem + 16;
+    b += 16 + sizeof(TileInfo) + 2 * sizeof(Agg) + 8 + 8 * (kPlanSmem + 1) + 4 * kPlanSmem + 32;
     return (b + 127) & ~size_t(127);
 }
 
@@ -1060,25 +1060,33 @@ static cudaError_t launch_count(const KArgs &a, const Plan &pl, int grid, int sm
     return launch_pdl(daq_count_kernel<TW, NS, HF>, grid, count_threads<NS>(), pl.smem, s, a);
 }
 
+// The compact kernel (DAQ_SPARSE: the form that passes over tiles without a
+// marked sample), grids from occupancy when grid <= 0.
+template <int TW, bool kSparse>
+static cudaError_t launch_compact(const KArgs &a, const Plan &pl, int grid, int sms, int64_t tiles, cudaStream_t s)
+{
+    static size_t conf[64] = {0};
+    cudaError_t e = ensure_smem(daq_compact_kernel<TW, kSparse>, pl.smem_b, conf);
+    if (e != cudaSuccess) return e;
+    if (grid <= 0) {
+        int per = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, daq_compact_kernel<TW, kSparse>, 256, pl.smem_b);
+        if (e != cudaSuccess) return e;
+        if (per < 1) return cudaErrorInvalidConfiguration;
+        grid = per * sms;
+    }
+    grid = (int)std::min<int64_t>(grid, tiles);
+    return launch_pdl(daq_compact_kernel<TW, kSparse>, grid, 256, pl.smem_b, s, a);
+}
+
 // Count pass, scan, compact pass.  Events (optional): [2] after the count
 // kernel, [3] after the scan, [4] after the compact kernel.
 template <int TW>
 static cudaError_t launch_twopass(const KArgs &a, const Plan &pl, int grid, int sms, bool skip_isl,
                                   cudaEvent_t const *ev, cudaStream_t s)
 {
-    static size_t conf_b[64] = {0};
-    cudaError_t e = ensure_smem(daq_compact_kernel<TW>, pl.smem_b, conf_b);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
     const int64_t tiles = std::max<int64_t>(1, pl.max_tiles);
-    int grid_b = grid;
-    if (grid <= 0) {
-        int per_b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_b, daq_compact_kernel<TW>, 256, pl.smem_b);
-        if (e != cudaSuccess) return e;
-        if (per_b < 1) return cudaErrorInvalidConfiguration;
-        grid_b = per_b * sms;
-    }
-    grid_b = (int)std::min<int64_t>(grid_b, tiles);
     e = pl.halo_free             ? launch_count<TW, 2, true>(a, pl, grid, sms, tiles, s)
         : pl.count_ns == 3       ? launch_count<TW, 3, false>(a, pl, grid, sms, tiles, s)
                                  : launch_count<TW, 2, false>(a, pl, grid, sms, tiles, s);
@@ -1089,7 +1097,11 @@ static cudaError_t launch_twopass(const KArgs &a, const Plan &pl, int grid, int 
                      : launch_pdl(daq_scan_kernel<TW, false>, scan_blocks, kScanThreads, 0, s, a);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
-    if (!skip_isl && (e = launch_pdl(daq_compact_kernel<TW>, grid_b, 256, pl.smem_b, s, a)) != cudaSuccess) return e;
+    if (!skip_isl) {
+        e = (a.flags & DAQ_SPARSE) ? launch_compact<TW, true>(a, pl, grid, sms, tiles, s)
+                                   : launch_compact<TW, false>(a, pl, grid, sms, tiles, s);
+        if (e != cudaSuccess) return e;
+    }
     if (ev && (e = cudaEventRecord(ev[4], s)) != cudaSuccess) return e;
     return cudaSuccess;
 }

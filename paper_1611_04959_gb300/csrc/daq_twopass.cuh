@@ -624,10 +624,17 @@ __device__ __forceinline__ void plain_tile_load_b(const KArgs &a, const TileInfo
 // current tile are written; the marks, record and prefix of the next tile are
 // loaded into registers at the same point.  The CTA takes tiles first, first +
 // G, ...; any block size that is a multiple of 32 and >= 128.
+// kSparse (DAQ_SPARSE): tiles without a marked sample (no rows, no island
+// starts: nothing to write) are passed over.  With the next tile's inputs
+// warp 0 also reads the record of the tile after it; when that tile has no
+// marked sample, warp 0 reads the records of the 32 tiles after it at once,
+// while the current tile's load lands, and leaves the first with one in
+// shared memory.  The default form keeps a fixed stride: on fills where
+// nearly every tile holds a marked sample the extra steps cost 0.5-1%.
 // kFused: a tile's marks, record and prefix are read once the scanner has
 // passed it (L1-bypassing loads: other CTAs wrote them during this launch), and
 // each tile staged is counted in the compacted counter.
-template <int TW, bool kFused>
+template <int TW, bool kFused, bool kSparse = false>
 __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem, long long first, long long G)
 {
     constexpr int NWT = TW / 32;
@@ -647,6 +654,8 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
     long long *fts_s = reinterpret_cast<long long *>(bar + 1);             // [kPlanSmem + 1]
     int32_t *lens_s = reinterpret_cast<int32_t *>(fts_s + kPlanSmem + 1);  // [kPlanSmem]
     uint32_t *s_boxes = reinterpret_cast<uint32_t *>(lens_s + kPlanSmem);  // boxes of the CTA's next tile
+    // kSparse: the CTA's next tile, when tile + G holds no marked sample
+    long long *s_next = reinterpret_cast<long long *>((reinterpret_cast<uintptr_t>(s_boxes + 1) + 7) & ~uintptr_t(7));
     const PlanView plan = cache_plan(a, fts_s, lens_s, tid, nthr);
     if (tid == 0) {
         mbar_init(bar, 1);
@@ -675,6 +684,33 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
         }
         return boxes;
     };
+    // kSparse, warp 0: the first of tiles t, t + G, ... that holds a marked
+    // sample (total if none) and its record flags, in every lane
+    auto find_next = [&](long long t, long long &nt, uint32_t &fl) {
+        for (;; t += 32 * G) {
+            if (t >= total) {
+                nt = total;
+                fl = 0u;
+                return;
+            }
+            const long long u = t + lane * G;
+            int m = 0;
+            uint32_t f = 0u;
+            if (u < total) {
+                const int4 rv = *reinterpret_cast<const int4 *>(recs + u);
+                m = rv.x;
+                f = (uint32_t)rv.w;
+            }
+            const uint32_t stop = __ballot_sync(kFull, u >= total || m != 0);
+            if (stop) {
+                const int k = __ffs(stop) - 1;
+                const long long v = t + (long long)k * G;
+                nt = v < total ? v : total;
+                fl = __shfl_sync(kFull, f, k);
+                return;
+            }
+        }
+    };
     auto start_load = [&](long long tile, uint32_t boxes) {  // one thread
         // no pedestal sum: the compact pass does not use it, and its load would
         // delay the bulk copy
@@ -688,9 +724,20 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
     };
 
     // warp 0's inputs of the next tile, in registers, and (lane 0) the record
-    // flags of the tile after it; false if the wait gave up
-    auto load_inputs = [&](long long tile, uint32_t &Mt, TileRec &r, TileExcl &e, uint32_t &fl2) -> bool {
-        fl2 = lane == 0 ? flags_of(tile + G) : 0u;
+    // flags of the tile after it (kSparse: and its marked samples); false if
+    // the wait gave up
+    auto load_inputs = [&](long long tile, uint32_t &Mt, TileRec &r, TileExcl &e, int &m2, uint32_t &fl2) -> bool {
+        if constexpr (kSparse) {
+            m2 = 1;
+            fl2 = 0u;
+            if (lane == 0 && tile + G < total) {
+                const int4 rv = *reinterpret_cast<const int4 *>(recs + tile + G);
+                m2 = rv.x;
+                fl2 = (uint32_t)rv.w;
+            }
+        } else {
+            fl2 = lane == 0 ? flags_of(tile + G) : 0u;
+        }
         if (kFused) {
             int ok = 1;
             if (lane == 0) ok = wait_counter_ge(a, scanned_ctr(a), (unsigned long long)tile + 1ull) ? 1 : 0;
@@ -714,6 +761,7 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
     bool store_pending = false;
     bool load_pending = false;  // thread 32 (single-launch form): a load issued that no thread has waited for
     uint32_t nMt = 0, nfl2 = 0;
+    int nm2 = 1;  // kSparse, lane 0 of warp 0: marked samples of the next tile + G
     TileRec nr{0, 0, 0, 0};
     TileExcl ne{0, 0, 0};
     int in_ok = 1;
@@ -722,17 +770,28 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
             start_load(first, boxes_of(flags_of(first)));
             load_pending = kFused;
         }
-        if (warp == 0) in_ok = load_inputs(first, nMt, nr, ne, nfl2) ? 1 : 0;
+        if (warp == 0) in_ok = load_inputs(first, nMt, nr, ne, nm2, nfl2) ? 1 : 0;
     }
-    for (long long tile = first; tile < total; tile += G) {
+    for (long long tile = first; tile < total;) {
+        int moved = 0;  // kSparse, warp 0: the next tile is not tile + G (it is in s_next)
         if (__syncthreads_or(!in_ok)) break;  // tinfo holds this tile; warp 0 has its inputs
         const TileInfo T = *tinfo;
         if (!a.use_tma) plain_tile_load_b(a, T, slot, tid, nthr);
         if (warp == 0) {
             const Agg g = words_from_marks<TW>(nMt, (nr.flags >> 1) & 1, (nr.flags >> 2) & 1,
                                                (int)(T.t_end - T.t0), W, nullptr, lane);
+            uint32_t fl = nfl2;
+            if constexpr (kSparse) {
+                if (tile + G < total && __shfl_sync(kFull, nm2, 0) == 0) {
+                    // tile + G holds no marked sample: find the CTA's next one
+                    long long nt;
+                    find_next(tile + 2 * G, nt, fl);
+                    moved = 1;
+                    if (lane == 0) *s_next = nt;
+                }
+            }
             if (lane == 0) {
-                *s_boxes = boxes_of(nfl2);  // read with this tile's inputs; the next load uses it
+                *s_boxes = boxes_of(fl);  // read with this tile's inputs; the next load uses it
                 Agg ex;
                 ex.m = ne.m;
                 ex.s = ne.s;
@@ -766,15 +825,20 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
         const int nt = (int)(T.t_end - T.t0);
         for (int it = warp; it < (nt + 63) / 64; it += nwarps)
             compact_step(a, smem_addr(slot), it, nt, W.m, W.mb, stage, phase, lane);
-        __syncthreads();  // rows staged; the slot is free
+        // rows staged; the slot is free
+        long long next = tile + G;
+        if constexpr (kSparse) {
+            if (__syncthreads_or(tid == 0 && moved)) next = *s_next;
+        } else {
+            __syncthreads();
+        }
         if (kFused && tid == 0) atomicAdd(compacted_ctr(a), 1ull);
-        const long long next = tile + G;
         if (next < total) {
             if (tid == 32) {
                 start_load(next, *s_boxes);
                 load_pending = kFused && a.use_tma;  // the single-launch form may stop before waiting for it
             }
-            if (warp == 0) in_ok = load_inputs(next, nMt, nr, ne, nfl2) ? 1 : 0;
+            if (warp == 0) in_ok = load_inputs(next, nMt, nr, ne, nm2, nfl2) ? 1 : 0;
         }
         if (tid == 0) trace_stamp(a, tile, 7);
         // rows [ex.m, ex.m + agg.m) <- stage bytes [phase, phase + agg.m * 2X)
@@ -815,18 +879,19 @@ __device__ __forceinline__ void compact_role(const KArgs &a, unsigned char *smem
         }
         if (warp == 0) write_headers<TW>(a, T, W, ex, lane);
         if (tid == 0) trace_stamp(a, tile, 9);
+        tile = next;
     }
     if (tid == 0 && store_pending) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     if (tid == 32 && load_pending) mbar_wait_bounded(bar, phase_bit, kWaitLimitNs);  // left early: let it land
 }
 
-template <int TW>
+template <int TW, bool kSparse>
 __global__ void __launch_bounds__(256, 2) daq_compact_kernel(const __grid_constant__ KArgs a)
 {
     pdl_wait();                // every tile's prefix
     if (aborted(a)) return;    // the scan gave up: its prefixes are incomplete
     extern __shared__ __align__(128) unsigned char smem[];
-    compact_role<TW, false>(a, smem, blockIdx.x, gridDim.x);
+    compact_role<TW, false, kSparse>(a, smem, blockIdx.x, gridDim.x);
 }
 
 // ============================================================================ single-launch form

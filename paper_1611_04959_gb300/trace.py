@@ -34,7 +34,10 @@ def summarize(tr: np.ndarray) -> dict:
     for a, b in STAGE_PAIRS:
         if not (tr[:, idx[a]] > 0).any() or not (tr[:, idx[b]] > 0).any():
             continue
-        d = (tr[:, idx[b]] - tr[:, idx[a]]) / 1e3
+        both = (tr[:, idx[a]] > 0) & (tr[:, idx[b]] > 0)  # tiles a pass skips carry none of its stamps
+        if not both.any():
+            continue
+        d = (tr[both, idx[b]] - tr[both, idx[a]]) / 1e3
         stages[f"{a}->{b}"] = {"p50_us": round(float(np.median(d)), 3), "p90_us": round(float(np.percentile(d, 90)), 3),
                                "max_us": round(float(d.max()), 3)}
     out["stages"] = stages
@@ -44,7 +47,8 @@ def summarize(tr: np.ndarray) -> dict:
         out["lookback_wait_polls_p50"] = float(np.median(lb % 100000))
         out["lookback_wait_polls_p90"] = float(np.percentile(lb % 100000, 90))
     # tiles in flight (ticket .. rows_written) sampled on a time grid
-    starts, ends = tr[:, idx["ticket"]] - t0, tr[:, idx["rows_written"]] - t0
+    done = tr[:, idx["rows_written"]] > 0
+    starts, ends = tr[done, idx["ticket"]] - t0, tr[done, idx["rows_written"]] - t0
     grid = np.linspace(0, ends.max(), 200)
     inflight = [(int(((starts <= g) & (ends > g)).sum())) for g in grid[20:180]]
     out["tiles_in_flight_p50"] = float(np.median(inflight))

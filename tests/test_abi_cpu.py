@@ -45,8 +45,8 @@ def test_struct_layouts_match_header(daq):
 
 
 def test_binding_layout_matches_the_c_compiler(daq, tmp_path):
-    """The ctypes mirror of daq_params and daq_islands has the sizes and field
-    offsets a C compiler gives the header's structs."""
+    """The ctypes mirrors of daq_params, daq_islands and daq_tune_result have
+    the sizes and field offsets a C compiler gives the header's structs."""
     import shutil
     import subprocess
     gcc = shutil.which("gcc")
@@ -55,21 +55,22 @@ def test_binding_layout_matches_the_c_compiler(daq, tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stddef.h>\n#include <stdio.h>\n#include "daq.h"\n'
-        'int main(void) { printf("%zu %zu %zu %zu %zu\\n", sizeof(daq_params), offsetof(daq_params, wait_limit_ns),'
-        ' offsetof(daq_params, lag_tiles), offsetof(daq_params, stream), sizeof(daq_islands)); return 0; }\n')
+        'int main(void) { printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(daq_params), offsetof(daq_params, wait_limit_ns),'
+        ' offsetof(daq_params, lag_tiles), offsetof(daq_params, stream), sizeof(daq_islands),'
+        ' sizeof(daq_tune_result), offsetof(daq_tune_result, flags)); return 0; }\n')
     exe = tmp_path / "layout"
     subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     P = daq.DaqParams
     assert got == [ctypes.sizeof(P), P.wait_limit_ns.offset, P.lag_tiles.offset, P.stream.offset,
-                   ctypes.sizeof(daq.DaqIslands)]
+                   ctypes.sizeof(daq.DaqIslands), ctypes.sizeof(daq.DaqTuneResult), daq.DaqTuneResult.flags.offset]
 
 
 def test_debug_checks_flag_and_status(daq):
     """DAQ_DEBUG_CHECKS is its own flag bit; a failed device index check
     (DAQ_DEV_BAD_INDEX) maps to DAQ_EINDEX, after timeouts and bad fill
     lengths and before capacity shortfalls."""
-    flags = [daq.DAQ_SKIP_Q, daq.DAQ_SKIP_ISLANDS, daq.DAQ_SYNC, daq.DAQ_PACK_POOL, daq.DAQ_DEBUG_CHECKS]
+    flags = [daq.DAQ_SKIP_Q, daq.DAQ_SKIP_ISLANDS, daq.DAQ_SYNC, daq.DAQ_PACK_POOL, daq.DAQ_DEBUG_CHECKS, daq.DAQ_SPARSE]
     assert len(set(flags)) == len(flags) and all(f & (f - 1) == 0 for f in flags)
     bits = [daq.DAQ_DEV_HDR_OVERFLOW, daq.DAQ_DEV_POOL_OVERFLOW, daq.DAQ_DEV_TIMEOUT, daq.DAQ_DEV_BAD_FILL_LEN,
             daq.DAQ_DEV_BAD_INDEX]

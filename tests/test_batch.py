@@ -93,8 +93,9 @@ def test_graph_replay_matches_oracle_and_accumulates_q(genv):
     assert int(q.abs().sum().item()) == 0          # creation leaves Q alone
     t = plan.tuning()
     assert t["n_tried"] >= 5 and not t["from_cache"] and t["ms"] > 0
-    assert (t["tile"], t["grid"]) in {(448, 0), (224, 0), (128, 0), (448, -4), (224, -4), (448, -1), (960, -1),
-                                      (448, -2), (448, -3)} or t["grid"] > 0
+    assert (t["tile"], t["grid"]) in {(0, 0), (448, 0), (224, 0), (128, 0), (448, -4), (224, -4), (448, -1),
+                                      (960, -1), (448, -2), (448, -3)} or t["grid"] > 0
+    assert t["flags"] in (0, daq.DAQ_SPARSE) and (t["flags"] == 0 or (t["tile"], t["grid"]) == (0, 0))
     stream = torch.cuda.Stream()
     for k in range(3):
         out.counts.zero_()
@@ -121,12 +122,13 @@ def test_tuning_cache_and_explicit_configuration(genv):
     a = daq.BatchPlan(x, q, out, fill_len=fl_d, tune=True, force=True, **params)
     b = daq.BatchPlan(x, q, out, fill_len=fl_d, tune=True, **params)
     ta, tb = a.tuning(), b.tuning()
-    assert tb["from_cache"] and tb["n_tried"] == 0 and (ta["tile"], ta["grid"]) == (tb["tile"], tb["grid"])
+    assert tb["from_cache"] and tb["n_tried"] == 0
+    assert (ta["tile"], ta["grid"], ta["flags"]) == (tb["tile"], tb["grid"], tb["flags"])
     a.close()
-    for tile, grid in [(224, -1), (128, 3), (448, -3)]:
-        c = daq.BatchPlan(x, q, out, fill_len=fl_d, tune=False, tile=tile, grid=grid, **params)
+    for tile, grid, flags in [(224, -1, 0), (128, 3, 0), (448, -3, 0), (0, 0, daq.DAQ_SPARSE), (224, 5, daq.DAQ_SPARSE)]:
+        c = daq.BatchPlan(x, q, out, fill_len=fl_d, tune=False, tile=tile, grid=grid, flags=flags, **params)
         tc = c.tuning()
-        assert (tc["tile"], tc["grid"]) == (tile, grid) and tc["n_tried"] == 0
+        assert (tc["tile"], tc["grid"], tc["flags"]) == (tile, grid, flags) and tc["n_tried"] == 0
         q.zero_()
         c.launch()
         torch.cuda.synchronize()

@@ -92,7 +92,33 @@ def test_random_shapes(env, seed):
     hr = (params["pre"] + 8) // 8 * 8
     if tile and tile + hl + hr > 1024:
         tile = 0
-    compare(env, s, params, fill_len=fill_len, tile=tile, grid=int(rng.choice([0, 0, -1, -2, -3, -4, -4, 2, -5, -5, -6, -6, -6])))
+    grid = int(rng.choice([0, 0, -1, -2, -3, -4, -4, 2, -5, -5, -6, -6, -6]))
+    flags = 32 if grid >= 0 and seed % 2 else 0  # DAQ_SPARSE on half the two-pass cases
+    compare(env, s, params, fill_len=fill_len, tile=tile, grid=grid, flags=flags)
+
+
+@pytest.mark.parametrize("grid", [1, 3, 0])
+@pytest.mark.parametrize("sparse", [True, False])
+def test_compact_passes_over_tiles_without_marks(env, grid, sparse):
+    """A sparse fill with stretches of flat samples (no crossing, no marks).
+    With DAQ_SPARSE the compact pass takes only tiles that hold a marked
+    sample, reading 32 records of a CTA's sequence at a time.  With grid = 1 one
+    CTA takes all 5,000 tiles and passes the flat stretch (tiles ~764 to
+    ~4,387) over many such reads; grid = 3 gives shorter sequences."""
+    from synth import workloads as W
+    w = W.scaled(W.SPARSE_FULL_FILL, n_calo=4)
+    s = env["synth"].generate(w.config())
+    # each crystal's integer pedestal over the first 100 samples: a sample at
+    # that value adds nothing to the pedestal-subtracted sum
+    P = ((s[:, :, :, :100].astype(np.int64).sum(-1) + 50) // 100).astype(np.int16)
+    s[0, 0, :, 448_000:] = P[0, 0][:, None]
+    s[0, 1, :, :] = P[0, 1][:, None]
+    s[0, 2, :, :] = P[0, 2][:, None]
+    s[0, 3, :, 100:280_000] = P[0, 3][:, None]
+    res, ref = compare(env, s, w.params(), grid=grid, flags=env["daq"].DAQ_SPARSE if sparse else 0)
+    isl = ref["islands"]
+    assert len(isl) > 100
+    assert not np.any((isl["calo"] == 1) | (isl["calo"] == 2))
 
 
 def test_uneven_batch_of_fills(env):
@@ -180,22 +206,24 @@ def test_fill_length_out_of_range_is_flagged(env):
     assert e.value.status == daq.DAQ_EINVAL
 
 
-@pytest.mark.parametrize("grid", [0, -4, -5, -6])
-def test_full_fill_24_calorimeters(env, grid):
-    """The benchmark workload itself (1.45 GB), full parity: two-pass, single-launch, streaming and single-read forms."""
+@pytest.mark.parametrize("grid,flags", [(0, 0), (0, 32), (-4, 0), (-5, 0), (-6, 0)])
+def test_full_fill_24_calorimeters(env, grid, flags):
+    """The benchmark workload itself (1.45 GB), full parity: two-pass (also with
+    DAQ_SPARSE = 32), single-launch, streaming and single-read forms."""
     from synth import workloads as W
     w = W.PLAIN_FULL_FILL
     s = env["synth"].generate(w.config())
-    compare(env, s, w.params(), n_threads=16, grid=grid)
+    compare(env, s, w.params(), n_threads=16, grid=grid, flags=flags)
 
 
-@pytest.mark.parametrize("grid", [0, -6])
-def test_sparse_regime(env, grid):
-    """Per-crystal noise 3/sqrt(54): islands cover ~8% of the fill."""
+@pytest.mark.parametrize("grid,flags", [(0, 0), (0, 32), (-6, 0)])
+def test_sparse_regime(env, grid, flags):
+    """Per-crystal noise 3/sqrt(54): islands cover ~8% of the fill (flags 32:
+    DAQ_SPARSE, the compact pass that passes over tiles without marks)."""
     from synth import workloads as W
     w = W.scaled(W.SPARSE_FULL_FILL, n_calo=3)
     s = env["synth"].generate(w.config())
-    res, ref = compare(env, s, w.params(), grid=grid)
+    res, ref = compare(env, s, w.params(), grid=grid, flags=flags)
     assert 0.02 < ref["n_rows"] / (3 * s.shape[3]) < 0.2
 
 
