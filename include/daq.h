@@ -609,7 +609,10 @@ int daq_crystal_sum(const int16_t *samples, int n_calo, int n_xtal, int64_t n_sa
  *                         out_cap bytes) on `stream`; *out_bytes (device
  *                         int64) receives the
  *                         stream's size - bytes past out_cap are not written,
- *                         so out_cap >= daq_pack_bound() is always enough.
+ *                         so out_cap >= daq_pack_bound() is always enough -
+ *                         or -1 when a copy of pool rows into shared memory
+ *                         did not land within 4 s (the stream is then not
+ *                         valid).
  * daq_unpack_pool         decode a stream of in_bytes bytes into device
  *                         pool_out[rows][n_xtal]; *err (device int32) is set
  *                         to 0, or to a non-zero code when the header does not

@@ -234,6 +234,10 @@ extern "C" int daq_process_fills_host(int n_calo, int n_xtal, int64_t n_samples,
             return;
         }
         const int64_t n = hp->psize_h[j];
+        if (n < 0) {  // the packing gave up (a block copy did not land)
+            rc = DAQ_ETIMEOUT;
+            return;
+        }
         const int64_t k = std::max<int64_t>(0, std::min(n, io->packed_host_cap - packed_at));
         if (k > 0 && cudaMemcpyAsync(io->packed_host + packed_at, static_cast<unsigned char *>(io->packed_dev) + ch[j].pk_off,
                                      (size_t)k, cudaMemcpyDeviceToHost, hp->d2h) != cudaSuccess)

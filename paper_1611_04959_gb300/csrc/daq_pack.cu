@@ -12,8 +12,11 @@
 // row differences of a crystal are small (noise, pulse edges) and a block's
 // crystal column typically needs a few bits per sample instead of 16.
 //
-// One warp per block; the block's rows are copied to shared memory as 16-byte
-// vectors.  The size pass puts lanes on crystal columns: a lane walks its
+// One warp per block at a time, blocks b, b + W, ... (W warps in the grid).
+// Each warp keeps two block buffers in shared memory: while it works on one,
+// a bulk copy (one instruction, completing on the buffer's mbarrier) brings
+// in its next block, so the global load latency overlaps the work.  The size
+// pass puts lanes on crystal columns: a lane walks its
 // column down the 32 rows OR-ing the zigzag differences (the bit length of the
 // OR is that of the maximum: the column's width) and the block's size
 // follows.  An exclusive scan of the block sizes (three kernels) gives the
@@ -34,6 +37,7 @@
 #include <cstdint>
 
 #include "daq.h"
+#include "daq_device.cuh"
 
 namespace daq_pack {
 
@@ -44,10 +48,27 @@ constexpr int kMaxX = 64;
 constexpr uint32_t kMagic = 0x50514144u;
 constexpr int kScanPer = 4;
 constexpr int kScanChunk = kThreads * kScanPer;
+constexpr uint64_t kWaitNs = 4000000000ull;  // a block copy not landed after this: give up (error word)
 
 __device__ __forceinline__ uint32_t zigzag(int32_t d) { return ((uint32_t)d << 1) ^ (uint32_t)(d >> 31); }
 
 __device__ __forceinline__ int32_t unzigzag(uint32_t z) { return (z & 1u) ? -(int32_t)((z + 1u) >> 1) : (int32_t)(z >> 1); }
+
+// Per 16-bit half, modulo 2^16: v - p (no borrow crosses the halves).
+__device__ __forceinline__ uint32_t sub16x2(uint32_t v, uint32_t p)
+{
+    return ((v | 0x80008000u) - (p & 0x7fff7fffu)) ^ ((v ^ ~p) & 0x80008000u);
+}
+
+// Per 16-bit half: zigzag(d) = 2d for d >= 0, -2d - 1 else, i.e. (d << 1) ^
+// (the half's sign spread over it); the sign comes from a byte permute that
+// replicates the top bit of bytes 1 and 3.
+__device__ __forceinline__ uint32_t zigzag16x2(uint32_t d)
+{
+    uint32_t sgn;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(sgn) : "r"(d), "r"(0u), "r"(0xbb99u));
+    return ((d << 1) & 0xfffefffeu) ^ sgn;
+}
 
 // A warp's shared rows: the block's 32 rows back to back (row pitch X), as in
 // the pool.  Reading one crystal down the rows strides X int16 per lane, which
@@ -73,6 +94,63 @@ __device__ __forceinline__ int load_block(const int16_t *pool, long long rows, i
     return nv;
 }
 
+// Per-warp pipeline of 32-row blocks in dynamic shared memory: two buffers
+// of 64 X bytes (a block's rows as in the pool), then `extra` bytes of the
+// caller's, then two mbarriers.  Blocks below nfull (32 real rows) come in by
+// bulk copy, one block ahead; the last block, when it is shorter, is copied by
+// the lanes with its padding rows.  `wait` returns false when a copy did not
+// land within kWaitNs; `drain` waits (bounded) for copies still in flight, so
+// that the warp may leave.
+struct BlockPipe {
+    unsigned char *base, *extra;
+    uint64_t *bar;
+    int bufb;               // bytes of one buffer (64 X)
+    uint32_t pend = 0;      // lane 0: buffers with a copy issued and not waited for
+    uint32_t par = 0;       // lane 0: bit s = phase parity of buffer s's pending copy
+    uint32_t next_par = 0;  // bit s = phase parity the next wait on buffer s expects
+
+    static __host__ __device__ size_t bytes(int X, int extra) { return 2 * 64 * (size_t)X + (size_t)extra + 16; }
+
+    __device__ BlockPipe(unsigned char *b, int X, int extra_bytes, int lane)
+        : base(b), extra(b + 128 * X), bar(reinterpret_cast<uint64_t *>(b + 128 * X + extra_bytes)), bufb(64 * X)
+    {
+        if (lane == 0) {
+            daq::mbar_init(bar, 1);
+            daq::mbar_init(bar + 1, 1);
+            daq::fence_mbar_init();
+        }
+        __syncwarp();
+    }
+    __device__ int16_t *buf(int s) const { return reinterpret_cast<int16_t *>(base + s * bufb); }
+    // lane 0: start the copy of full block b into buffer s (the warp is done with it)
+    __device__ void issue(const int16_t *pool, int X, long long b, int s)
+    {
+        daq::fence_proxy_async_smem();
+        daq::mbar_arrive_expect_tx(bar + s, (uint32_t)bufb);
+        daq::bulk_g2s(buf(s), pool + 32ll * b * X, (uint32_t)bufb, bar + s);
+        pend |= 1u << s;
+        par = (par & ~(1u << s)) | (next_par & (1u << s));
+    }
+    // every lane: block b's rows are in buffer s
+    __device__ bool wait(const int16_t *pool, long long rows, int X, long long b, long long nfull, int s, int lane)
+    {
+        if (b < nfull) {
+            if (!daq::mbar_wait_bounded(bar + s, (next_par >> s) & 1u, kWaitNs)) return false;
+            next_par ^= 1u << s;
+            pend &= ~(1u << s);
+        } else {
+            load_block(pool, rows, X, b, buf(s), lane);
+        }
+        return true;
+    }
+    // lane 0: wait (bounded) for copies still in flight, so that the warp may leave
+    __device__ void drain()
+    {
+        for (int s = 0; s < 2; ++s)
+            if (pend & (1u << s)) daq::mbar_wait_bounded(bar + s, (par >> s) & 1u, kWaitNs);
+    }
+};
+
 // Block sizes, and the width of every crystal column (widths[b][x]).  Lanes
 // take crystal columns here: lane x walks its column down the block's 32 rows
 // (consecutive lanes read consecutive samples of a row: no bank conflict),
@@ -81,13 +159,22 @@ __device__ __forceinline__ int load_block(const int16_t *pool, long long rows, i
 // reduction of its own.
 __global__ void __launch_bounds__(kThreads) pack_size_kernel(const int16_t *pool, long long rows, int X,
                                                              long long nb, unsigned long long *sizes,
-                                                             uint8_t *widths)
+                                                             uint8_t *widths, int *perr)
 {
-    __shared__ __align__(16) int16_t sm_all[kWarps][kBlockElems];
+    extern __shared__ __align__(16) unsigned char dsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int16_t *sm = sm_all[warp];
-    for (long long b = (long long)blockIdx.x * kWarps + warp; b < nb; b += (long long)gridDim.x * kWarps) {
-        load_block(pool, rows, X, b, sm, lane);
+    BlockPipe pipe(dsm + warp * BlockPipe::bytes(X, 0), X, 0, lane);
+    const long long nfull = rows / 32, W = (long long)gridDim.x * kWarps;
+    long long b = (long long)blockIdx.x * kWarps + warp;
+    if (lane == 0 && b < nfull) pipe.issue(pool, X, b, 0);
+    for (int it = 0; b < nb; b += W, ++it) {
+        const int s = it & 1;
+        if (lane == 0 && b + W < nfull) pipe.issue(pool, X, b + W, s ^ 1);
+        if (!pipe.wait(pool, rows, X, b, nfull, s, lane)) {
+            if (lane == 0) atomicOr(perr, 1);
+            break;
+        }
+        const int16_t *sm = pipe.buf(s);
         unsigned words = 0;
         for (int x = lane; x < X; x += 32) {
             const int16_t *col = sm + x;
@@ -107,6 +194,7 @@ __global__ void __launch_bounds__(kThreads) pack_size_kernel(const int16_t *pool
         if (lane == 0) sizes[b] = 4ull * words;
         __syncwarp();
     }
+    if (lane == 0) pipe.drain();
 }
 
 // ------------------------------------------------------------------ exclusive scan of the block sizes
@@ -163,7 +251,7 @@ __global__ void __launch_bounds__(1024) scan_top_kernel(unsigned long long *chun
 __global__ void __launch_bounds__(kThreads) scan_apply_kernel(const unsigned long long *v, long long n,
                                                               const unsigned long long *chunk,
                                                               unsigned long long *offs, unsigned char *out,
-                                                              long long cap, long long *out_bytes)
+                                                              long long cap, long long *out_bytes, const int *perr)
 {
     __shared__ unsigned long long s[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -190,7 +278,7 @@ __global__ void __launch_bounds__(kThreads) scan_apply_kernel(const unsigned lon
         if (k <= n) {
             offs[k] = pre;
             if (table + 8 * k + 8 <= cap) reinterpret_cast<unsigned long long *>(out + table)[k] = pre;
-            if (k == n) *out_bytes = 16 + 8 * (n + 1) + (long long)pre;
+            if (k == n) *out_bytes = *perr ? -1 : 16 + 8 * (n + 1) + (long long)pre;  // -1: the size pass gave up
         }
         pre += loc[i];
     }
@@ -241,16 +329,19 @@ struct Transpose {
 //   before g (w4 = the four widths as bytes); lane 0 broadcasts the first
 //   samples two to a word.
 // - Alone (a width of 16 or 17: a difference of at least 2^14).
-__global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *pool, long long rows, int X, long long nb,
+// kPairs (even X): in the four-column path a lane reads its row's crystals two
+// to a 32-bit word and forms both differences and zigzag codes at once, in
+// 16-bit halves (exact there: every difference is within +-64).
+// A block copy that does not land within kWaitNs sets *out_bytes to -1.
+template <bool kPairs>
+__global__ void __launch_bounds__(kThreads, 4) pack_write_kernel(const int16_t *pool, long long rows, int X, long long nb,
                                                               const unsigned long long *offs, const uint8_t *widths,
-                                                              unsigned char *out, long long cap)
+                                                              unsigned char *out, long long cap, long long *out_bytes)
 {
-    __shared__ __align__(16) int16_t sm_all[kWarps][kBlockElems];
-    __shared__ __align__(16) uint8_t w_all[kWarps][kMaxX];
+    extern __shared__ __align__(16) unsigned char dsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int16_t *sm = sm_all[warp];
-    uint8_t *wsm = w_all[warp];
-    const int16_t *row = sm + lane * X;
+    BlockPipe pipe(dsm + warp * BlockPipe::bytes(X, kMaxX), X, kMaxX, lane);
+    uint8_t *wsm = pipe.extra;  // widths of the block being written
     const Transpose transpose(lane);
     const int k16 = lane & 15, k8 = lane & 7;
     const bool hi16 = lane >= 16;
@@ -262,9 +353,31 @@ __global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *poo
         out32[1] = (uint32_t)X;
         reinterpret_cast<unsigned long long *>(out)[1] = (unsigned long long)rows;
     }
-    for (long long b = (long long)blockIdx.x * kWarps + warp; b < nb; b += (long long)gridDim.x * kWarps) {
-        for (int x = lane; x < X; x += 32) wsm[x] = widths[b * X + x];
-        load_block(pool, rows, X, b, sm, lane);  // ends with __syncwarp
+    const long long nfull = rows / 32, Wn = (long long)gridDim.x * kWarps;
+    long long b = (long long)blockIdx.x * kWarps + warp;
+    int w_lo = 0, w_hi = 0;  // widths of columns lane and lane + 32 of the block to come
+    auto widths_of = [&](long long bb) {
+        w_lo = lane < X ? widths[bb * X + lane] : 0;
+        w_hi = lane + 32 < X ? widths[bb * X + lane + 32] : 0;
+    };
+    if (b < nb) {
+        if (lane == 0 && b < nfull) pipe.issue(pool, X, b, 0);
+        widths_of(b);
+    }
+    for (int it = 0; b < nb; b += Wn, ++it) {
+        const int s = it & 1;
+        if (lane < X) wsm[lane] = (uint8_t)w_lo;
+        if (lane + 32 < X) wsm[lane + 32] = (uint8_t)w_hi;
+        if (b + Wn < nb) {
+            if (lane == 0 && b + Wn < nfull) pipe.issue(pool, X, b + Wn, s ^ 1);
+            widths_of(b + Wn);
+        }
+        if (!pipe.wait(pool, rows, X, b, nfull, s, lane)) {
+            if (lane == 0) *out_bytes = -1;
+            break;
+        }
+        __syncwarp();
+        const int16_t *row = pipe.buf(s) + lane * X;
         const long long start = head + (long long)offs[b];  // bytes, a multiple of 4
         uint32_t *dst = out32 + (start >> 2);
         // words that may be written from the block's start (a block is < 2^11 words)
@@ -305,14 +418,26 @@ __global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *poo
                 pair(x + 2);
                 continue;
             }
-            const int32_t v0 = row[x], v1 = row[x + 1], v2 = row[x + 2], v3 = row[x + 3];
-            const uint32_t z0 = zigzag(v0 - __shfl_up_sync(kFull, v0, 1));
-            const uint32_t z1 = zigzag(v1 - __shfl_up_sync(kFull, v1, 1));
-            const uint32_t z2 = zigzag(v2 - __shfl_up_sync(kFull, v2, 1));
-            const uint32_t z3 = zigzag(v3 - __shfl_up_sync(kFull, v3, 1));
-            const uint32_t planes = transpose((z0 << 1) | (z1 << 9) | (z2 << 17) | (z3 << 25));
-            const uint32_t f01 = __shfl_sync(kFull, (uint32_t)(uint16_t)v0 | ((uint32_t)v1 << 16), 0);
-            const uint32_t f23 = __shfl_sync(kFull, (uint32_t)(uint16_t)v2 | ((uint32_t)v3 << 16), 0);
+            uint32_t zq, f01, f23;  // the four z << 1 as bytes; lane 0's samples two to a word
+            if constexpr (kPairs) {
+                const uint32_t *row32 = reinterpret_cast<const uint32_t *>(row);
+                const uint32_t v01 = row32[x >> 1], v23 = row32[(x >> 1) + 1];
+                const uint32_t z01 = zigzag16x2(sub16x2(v01, __shfl_up_sync(kFull, v01, 1)));
+                const uint32_t z23 = zigzag16x2(sub16x2(v23, __shfl_up_sync(kFull, v23, 1)));
+                zq = __byte_perm(z01, z23, 0x6420) << 1;  // z < 128: no bit crosses into the next byte
+                f01 = __shfl_sync(kFull, v01, 0);
+                f23 = __shfl_sync(kFull, v23, 0);
+            } else {
+                const int32_t v0 = row[x], v1 = row[x + 1], v2 = row[x + 2], v3 = row[x + 3];
+                const uint32_t z0 = zigzag(v0 - __shfl_up_sync(kFull, v0, 1));
+                const uint32_t z1 = zigzag(v1 - __shfl_up_sync(kFull, v1, 1));
+                const uint32_t z2 = zigzag(v2 - __shfl_up_sync(kFull, v2, 1));
+                const uint32_t z3 = zigzag(v3 - __shfl_up_sync(kFull, v3, 1));
+                zq = (z0 << 1) | (z1 << 9) | (z2 << 17) | (z3 << 25);
+                f01 = __shfl_sync(kFull, (uint32_t)(uint16_t)v0 | ((uint32_t)v1 << 16), 0);
+                f23 = __shfl_sync(kFull, (uint32_t)(uint16_t)v2 | ((uint32_t)v3 << 16), 0);
+            }
+            const uint32_t planes = transpose(zq);
             const uint32_t fp = g4 < 2 ? f01 : f23;
             const uint32_t w = (w4 >> g8) & 0xffu;
             const uint32_t hw = ((g4 & 1) ? fp >> 16 : fp & 0xffffu) | (w << 16);
@@ -325,6 +450,7 @@ __global__ void __launch_bounds__(kThreads) pack_write_kernel(const int16_t *poo
         if (x < X) single(x);
         __syncwarp();
     }
+    if (lane == 0) pipe.drain();
 }
 
 __global__ void __launch_bounds__(kThreads) unpack_kernel(const unsigned char *in, long long in_bytes, long long rows,
@@ -432,6 +558,37 @@ __global__ void __launch_bounds__(kThreads) unpack_kernel(const unsigned char *i
     }
 }
 
+// Grid of a pipelined kernel: every CTA resident at once (its warps step
+// through blocks), at most one warp per block.  The kernel's dynamic
+// shared-memory limit is raised once per device to what the largest n_xtal
+// needs (smem_max; a later call must never lower it), and the resident count
+// is found once per (kernel slot, device, n_xtal) and kept.
+constexpr int kGridDevices = 16;
+int g_resident[3][kGridDevices][kMaxX + 1] = {};  // CTAs resident per GPU, 0 = not known yet
+bool g_limit_set[3][kGridDevices] = {};
+
+template <typename K> int pipelined_grid(int slot, K kernel, int X, size_t smem, size_t smem_max, long long nb)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    int resident = dev < kGridDevices ? g_resident[slot][dev][X] : 0;
+    if (resident == 0) {
+        int sms = 0, per = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 0;
+        if (dev >= kGridDevices || !g_limit_set[slot][dev]) {
+            if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max) != cudaSuccess)
+                return 0;
+            if (dev < kGridDevices) g_limit_set[slot][dev] = true;
+        }
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, smem) != cudaSuccess || per < 1)
+            return 0;
+        resident = per * sms;
+        if (dev < kGridDevices) g_resident[slot][dev][X] = resident;
+    }
+    const long long want = (nb + kWarps - 1) / kWarps;
+    return (int)std::max<long long>(1, std::min<long long>(want, (long long)resident));
+}
+
 int grid_blocks(long long nb)
 {
     int dev = 0, sms = 0;
@@ -442,7 +599,7 @@ int grid_blocks(long long nb)
 }
 
 struct PackWs {
-    size_t sizes, offs, chunk, widths, total;
+    size_t sizes, offs, chunk, widths, err, total;
 };
 
 PackWs pack_ws(long long nb, int X)
@@ -454,7 +611,8 @@ PackWs pack_ws(long long nb, int X)
     w.chunk = up(w.offs + 8 * (size_t)(nb + 1));
     const long long n_chunks = (nb + kScanChunk - 1) / kScanChunk;
     w.widths = up(w.chunk + 8 * (size_t)(n_chunks + 1));
-    w.total = up(w.widths + (size_t)std::max<long long>(nb, 1) * (size_t)X);
+    w.err = up(w.widths + (size_t)std::max<long long>(nb, 1) * (size_t)X);
+    w.total = up(w.err + sizeof(int));
     return w;
 }
 
@@ -495,16 +653,27 @@ int daq_pack_pool(const int16_t *pool, int64_t rows, int n_xtal, void *out, int6
     auto *offs = reinterpret_cast<unsigned long long *>(ws + w.offs);
     auto *chunk = reinterpret_cast<unsigned long long *>(ws + w.chunk);
     auto *widths = reinterpret_cast<uint8_t *>(ws + w.widths);
+    auto *perr = reinterpret_cast<int *>(ws + w.err);
     unsigned char *o = static_cast<unsigned char *>(out);
     const long long n_apply = nb / kScanChunk + 1;  // blocks covering entries 0..nb
-    if (nb > 0) pack_size_kernel<<<grid_blocks(nb), kThreads, 0, s>>>(pool, rows, n_xtal, nb, sizes, widths);
+    const size_t smem_size = kWarps * BlockPipe::bytes(n_xtal, 0);
+    const size_t smem_write = kWarps * BlockPipe::bytes(n_xtal, kMaxX);
+    const bool pairs = (n_xtal % 2) == 0;
+    const auto write_kernel = pairs ? pack_write_kernel<true> : pack_write_kernel<false>;
+    const size_t max_size = kWarps * BlockPipe::bytes(kMaxX, 0), max_write = kWarps * BlockPipe::bytes(kMaxX, kMaxX);
+    const int g_size = nb > 0 ? pipelined_grid(0, pack_size_kernel, n_xtal, smem_size, max_size, nb) : 1;
+    const int g_write = pipelined_grid(pairs ? 1 : 2, write_kernel, n_xtal, smem_write, max_write,
+                                       std::max<long long>(nb, 1));
+    if (g_size < 1 || g_write < 1) return DAQ_ECUDA;
+    if (cudaMemsetAsync(perr, 0, sizeof(int), s) != cudaSuccess) return DAQ_ECUDA;
+    if (nb > 0) pack_size_kernel<<<g_size, kThreads, smem_size, s>>>(pool, rows, n_xtal, nb, sizes, widths, perr);
     if (nb > 0) scan_reduce_kernel<<<(unsigned)((nb + kScanChunk - 1) / kScanChunk), kThreads, 0, s>>>(sizes, nb, chunk);
     else if (cudaMemsetAsync(chunk, 0, 8, s) != cudaSuccess) return DAQ_ECUDA;
     scan_top_kernel<<<1, 1024, 0, s>>>(chunk, nb > 0 ? (nb + kScanChunk - 1) / kScanChunk : 0);
     scan_apply_kernel<<<(unsigned)n_apply, kThreads, 0, s>>>(sizes, nb, chunk, offs, o, out_cap,
-                                                             reinterpret_cast<long long *>(out_bytes));
-    pack_write_kernel<<<grid_blocks(std::max<long long>(nb, 1)), kThreads, 0, s>>>(pool, rows, n_xtal, nb, offs,
-                                                                                   widths, o, out_cap);
+                                                             reinterpret_cast<long long *>(out_bytes), perr);
+    write_kernel<<<g_write, kThreads, smem_write, s>>>(pool, rows, n_xtal, nb, offs, widths, o, out_cap,
+                                                       reinterpret_cast<long long *>(out_bytes));
     return cudaGetLastError() == cudaSuccess ? DAQ_OK : DAQ_ECUDA;
 }
 

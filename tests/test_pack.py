@@ -64,6 +64,19 @@ def test_stream_matches_oracle_and_round_trips(env, rows, X):
 
 
 @pytest.mark.gpu
+def test_crystal_counts_in_any_order(env):
+    """The packing kernels size their shared memory by the crystal count: calls
+    with a large, a small and again the large count, in one process, all run
+    and match the oracle (a smaller call must not lower the kernels' limit)."""
+    torch, daq, oracle = env["torch"], env["daq"], env["oracle"]
+    for k, (rows, X) in enumerate([(4000, 64), (300, 1), (70, 2), (4000, 64), (1000, 54), (33, 3), (1000, 54)]):
+        rng = np.random.default_rng(900 + k)
+        pool = (1800 + np.cumsum(rng.integers(-9, 10, size=(rows, X)), axis=0)).astype(np.int16)
+        got, n = daq.pack_pool(torch.from_numpy(pool).cuda(), rows)
+        assert np.array_equal(got.cpu().numpy(), oracle.pack(pool)), (rows, X)
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("rows,X", [(777, 54), (4096 + 13, 7), (2000, 64), (1500, 9)])
 def test_every_width_class_and_mix(env, rows, X):
     """Columns whose row-to-row steps span every width class: <= 7 bits (four
