@@ -316,6 +316,17 @@ struct Transpose {
         }
         return x;
     }
+    // two independent transposes, stage by stage (their shuffles overlap)
+    __device__ __forceinline__ void two(uint32_t &x, uint32_t &z) const
+    {
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            const uint32_t y = __shfl_xor_sync(kFull, x, 16 >> t);
+            const uint32_t w = __shfl_xor_sync(kFull, z, 16 >> t);
+            x = (x & keep[t]) | (__funnelshift_l(y, y, rot[t]) & ~keep[t]);
+            z = (z & keep[t]) | (__funnelshift_l(w, w, rot[t]) & ~keep[t]);
+        }
+    }
 };
 
 // Crystal columns go through the transpose four at a time when all four
@@ -410,15 +421,8 @@ __global__ void __launch_bounds__(kThreads, 4) pack_write_kernel(const int16_t *
             if (k16 <= w && i < room) dst[i] = k16 ? planes : hw;
             o += 2 + wa + wb;
         };
-        int x = 0;
-        for (; x + 3 < X; x += 4) {
-            const uint32_t w4 = *reinterpret_cast<const uint32_t *>(wsm + x);
-            if ((w4 + 0x78787878u) & 0x80808080u) {  // a width above 7
-                pair(x);
-                pair(x + 2);
-                continue;
-            }
-            uint32_t zq, f01, f23;  // the four z << 1 as bytes; lane 0's samples two to a word
+        // four columns of width <= 7: their z << 1 as bytes, lane 0's samples two to a word
+        auto quad_z = [&](int x, uint32_t &zq, uint32_t &f01, uint32_t &f23) {
             if constexpr (kPairs) {
                 const uint32_t *row32 = reinterpret_cast<const uint32_t *>(row);
                 const uint32_t v01 = row32[x >> 1], v23 = row32[(x >> 1) + 1];
@@ -437,7 +441,9 @@ __global__ void __launch_bounds__(kThreads, 4) pack_write_kernel(const int16_t *
                 f01 = __shfl_sync(kFull, (uint32_t)(uint16_t)v0 | ((uint32_t)v1 << 16), 0);
                 f23 = __shfl_sync(kFull, (uint32_t)(uint16_t)v2 | ((uint32_t)v3 << 16), 0);
             }
-            const uint32_t planes = transpose(zq);
+        };
+        // store the words of four columns (widths w4 as bytes) from their transposed planes
+        auto quad_store = [&](uint32_t planes, uint32_t w4, uint32_t f01, uint32_t f23) {
             const uint32_t fp = g4 < 2 ? f01 : f23;
             const uint32_t w = (w4 >> g8) & 0xffu;
             const uint32_t hw = ((g4 & 1) ? fp >> 16 : fp & 0xffffu) | (w << 16);
@@ -445,7 +451,35 @@ __global__ void __launch_bounds__(kThreads, 4) pack_write_kernel(const int16_t *
             const int i = o + (int)((before >> g8) & 0xffu) + k8;
             if (k8 <= (int)w && i < room) dst[i] = k8 ? planes : hw;
             o += (int)(before >> 24) + 1 + (int)(w4 >> 24);
+        };
+        auto narrow = [](uint32_t w4) { return ((w4 + 0x78787878u) & 0x80808080u) == 0u; };  // every width <= 7
+        auto group = [&](int x, uint32_t w4) {
+            if (!narrow(w4)) {
+                pair(x);
+                pair(x + 2);
+                return;
+            }
+            uint32_t zq, f01, f23;
+            quad_z(x, zq, f01, f23);
+            quad_store(transpose(zq), w4, f01, f23);
+        };
+        int x = 0;
+        for (; x + 7 < X; x += 8) {  // two groups of four: both narrow, their transposes overlap
+            const uint32_t w4a = *reinterpret_cast<const uint32_t *>(wsm + x);
+            const uint32_t w4b = *reinterpret_cast<const uint32_t *>(wsm + x + 4);
+            if (narrow(w4a) && narrow(w4b)) {
+                uint32_t za, fa01, fa23, zb, fb01, fb23;
+                quad_z(x, za, fa01, fa23);
+                quad_z(x + 4, zb, fb01, fb23);
+                transpose.two(za, zb);
+                quad_store(za, w4a, fa01, fa23);
+                quad_store(zb, w4b, fb01, fb23);
+            } else {
+                group(x, w4a);
+                group(x + 4, w4b);
+            }
         }
+        for (; x + 3 < X; x += 4) group(x, *reinterpret_cast<const uint32_t *>(wsm + x));
         for (; x + 1 < X; x += 2) pair(x);
         if (x < X) single(x);
         __syncwarp();
