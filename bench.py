@@ -554,7 +554,8 @@ def bench_batched(args, torch, dev, daq, synth, W) -> dict:
            "raw_bytes_per_batch": raw, "islands_per_batch": int(counts[0]), "pool_rows_per_batch": int(counts[1]),
            "coverage": round(int(counts[1]) / rows, 4),
            "launch": "one CUDA graph launch per batch (daq_batch_plan_create / daq_batch_launch)",
-           "tuned": {"tile": tuning["tile"], "grid": tuning["grid"], "candidates": tuning["n_tried"],
+           "tuned": {"tile": tuning["tile"], "grid": tuning["grid"], "flags": tuning.get("flags", 0),
+                     "candidates": tuning["n_tried"],
                      "ms": round(tuning["ms"], 4), "ms_default_config": round(tuning["ms_default"], 4),
                      "tuning_s": round(tune_s, 2)},
            "gpu_launches": 4 * Kb, "generation_s": round(gen_s, 1),
