@@ -95,7 +95,9 @@ __device__ __forceinline__ int load_block(const int16_t *pool, long long rows, i
 }
 
 // Per-warp pipeline of 32-row blocks in dynamic shared memory: two buffers
-// of 64 X bytes (a block's rows as in the pool), then `extra` bytes of the
+// of 64 X bytes (a block's rows back to back, row pitch X, as in the pool:
+// reading one crystal down the rows strides X int16 per lane, conflict-free
+// whenever X/2 is odd, as for 54 crystals), then `extra` bytes of the
 // caller's, then two mbarriers.  Blocks below nfull (32 real rows) come in by
 // bulk copy, one block ahead; the last block, when it is shorter, is copied by
 // the lanes with its padding rows.  `wait` returns false when a copy did not
