@@ -109,6 +109,18 @@ def test_pipelined_host_form_matches_oracle(env, F, C, N, locked_out):
     check(run_host(env, s, w.params(), locked_out=locked_out), ref)
 
 
+@pytest.mark.parametrize("pack", [False, True])
+def test_host_form_passes_the_sparse_flag_through(env, pack):
+    """DAQ_SPARSE reaches every chunk's processing: a sparse fill through the
+    host form, plain and packed, matches the oracle."""
+    from synth import workloads as W
+    w = W.scaled(W.SPARSE_FULL_FILL, n_calo=3)
+    s = env["synth"].generate(w.config())
+    ref = env["oracle"].process_fills(s, w.params(), n_threads=8)
+    assert 0 < ref["n_rows"] < 0.2 * s.shape[1] * s.shape[3]
+    check(run_host(env, s, dict(w.params(), flags=env["daq"].DAQ_SPARSE), pack=pack), ref)
+
+
 def test_host_form_with_fill_lengths_and_two_decimations(env):
     from synth import workloads as W
     w = W.scaled(W.STRESS, n_fills=4, n_calo=3, n_samples=24_000)
