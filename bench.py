@@ -413,6 +413,7 @@ def bench_gb300(args, ws, rank, local):
     # ---- sparse regime: islands cover ~8% of the fill
     if not args.no_sparse and not args.quick:
         result["sparse"] = bench_sparse(args, torch, dev, daq, synth, W)
+        result["sparse"]["forms"] = bench_sparse_forms(args, torch, dev, daq, synth, W)
 
     # ---- lossless packing of the pool rows
     if not args.no_pack and not args.quick:
@@ -466,12 +467,14 @@ def bench_gb300(args, ws, rank, local):
     return result if rank == 0 else None
 
 
-def bench_batched(args, torch, dev, daq, synth, W) -> dict:
+def bench_batched(args, torch, dev, daq, synth, W, w=None, plain_flags=0) -> dict:
     """The batching workload: 16 fills x 24 calorimeters, lengths uniform in
     [80k, 560k] samples and pulse rates x log-uniform[0.2, 5], processed by
-    one tuned plan replayed as a CUDA graph; Q accumulates over the fills."""
+    one tuned plan replayed as a CUDA graph; Q accumulates over the fills.
+    `w` replaces the workload (same shape); plain_flags are the plain form's
+    processing flags (the tuned plan chooses its own)."""
     import numpy as np
-    w = W.BATCH_UNEVEN
+    w = W.BATCH_UNEVEN if w is None else w
     params = w.params()
     fl, rate = w.plan()
     F, C, X, N = w.n_fills, w.n_calo, 54, w.n_samples
@@ -515,7 +518,7 @@ def bench_batched(args, torch, dev, daq, synth, W) -> dict:
     # the plain form on the same fills: the default kernels (two-pass, library
     # tile), one daq_process_fills call per fill, no graph and no tuning; each
     # call writes its fill's records and rows from the start of the outputs
-    pp = daq.make_params(**params, stream=stream)
+    pp = daq.make_params(**params, stream=stream, flags=plain_flags)
     wsb1 = daq.daq_workspace_size(C, X, N, 1, pp)
     ws1 = torch.empty(wsb1, dtype=torch.uint8, device=dev)
     pp.workspace, pp.workspace_bytes = ws1.data_ptr(), wsb1
@@ -543,14 +546,15 @@ def bench_batched(args, torch, dev, daq, synth, W) -> dict:
     plain = {"value": round(Kb * raw / (plain_ms * 1e-3) / 1e9, 2), "unit": UNIT, "steps": Kb,
              "ms_per_batch": round(plain_ms / Kb, 4),
              "form": "default two-pass kernels, one daq_process_fills call per fill (16 calls per batch), "
-                     "no graph, no tuning"}
+                     "no graph, no tuning" + (f", flags {plain_flags}" if plain_flags else "")}
     del ws1
     res = {"value": round(Kb * raw / (total_ms * 1e-3) / 1e9, 2), "unit": UNIT, "steps": Kb,
            "ms_per_batch": round(total_ms / Kb, 4),
            "latency_ms": {"p50": round(statistics.median(ms), 4), "p99": round(float(np.percentile(ms, 99)), 4)},
            "pct_of_hbm_peak": round(100.0 * Kb * raw / (total_ms * 1e-3) / 1e9 / measured_peaks()[0], 2),
            "workload": "16 fills x 24 calorimeters x 54 crystals, lengths uniform in [80k, 560k] samples "
-                       "(pitch 560,000), pulse rate x log-uniform[0.2, 5] per fill, T=30, pre=8, post=24, D=32",
+                       "(pitch 560,000), pulse rate x log-uniform[0.2, 5] per fill, T=30, pre=8, post=24, D=32"
+                       + ("" if w is W.BATCH_UNEVEN else f"; {w.name}"),
            "raw_bytes_per_batch": raw, "islands_per_batch": int(counts[0]), "pool_rows_per_batch": int(counts[1]),
            "coverage": round(int(counts[1]) / rows, 4),
            "launch": "one CUDA graph launch per batch (daq_batch_plan_create / daq_batch_launch)",
@@ -962,6 +966,70 @@ def bench_served(args, torch, dev, daq, synth, W, samples0) -> dict:
                           "latency_ms_p50": round(sm.latency_p50_us / 1e3, 3)},
             "q": "one int64 Q histogram resident on the device across every served fill",
             "host_input": host_rates}
+
+
+def bench_sparse_forms(args, torch, dev, daq, synth, W) -> dict:
+    """The batched and served forms in the sparse regime (per-crystal noise
+    3/sqrt(54): islands on a few percent of the samples): the batching
+    workload's 16 uneven fills with that noise under a tuned plan, and a served
+    stream of sparse fills with DAQ_SPARSE at 10x and saturated."""
+    import math
+    import numpy as np
+    sig = 3.0 / math.sqrt(54.0)
+    import dataclasses
+    wb = dataclasses.replace(W.scaled(W.BATCH_UNEVEN, noise_sigma=sig), name="per-crystal noise sigma 3/sqrt(54)")
+    out = {"batched": bench_batched(args, torch, dev, daq, synth, W, w=wb, plain_flags=daq.DAQ_SPARSE)}
+    torch.cuda.empty_cache()
+    w = W.SPARSE_FULL_FILL
+    params = w.params()
+    C, X, N = w.n_calo, 54, w.n_samples
+    n_pool = max(1, args.serve_pool)
+    cfg = W.scaled(w, n_fills=n_pool).config()
+    pool = []
+    stage = torch.empty((1, C, X, N), dtype=torch.int16).pin_memory()
+    for f in range(n_pool):
+        synth.generate(cfg, out=stage.numpy(), n_threads=os.cpu_count() or 1, fills=(f, 1))
+        pool.append(stage[0].to(dev))
+    del stage
+    srv = daq.DaqServer(C, X, N, 40 << 30, **params, n_streams=4, auto_release=True, device=dev,
+                        flags=daq.DAQ_SPARSE)
+    for k in range(4):
+        srv.submit(pool[k % n_pool])
+    srv.drain(120.0)
+    srv.records(clear=True)
+    n = args.serve_fills
+    t0 = srv.now_us() + 50e3
+    arr = burst_schedule(n, 10, t0)
+    with ClockSampler(dev.index or 0) as clk:
+        for i, a in enumerate(arr):
+            srv.submit(pool[i % n_pool], arrival_us=a)
+        srv.drain(600.0)
+    recs = srv.records(clear=True)
+    assert all(r.status == 0 for r in recs), "served sparse fill failed"
+    sm = daq.daq_serving_summarize(recs)
+    n_sat = args.serve_fills_saturated
+    for i in range(n_sat):
+        srv.submit(pool[i % n_pool])
+    srv.drain(600.0)
+    recs_s = srv.records(clear=True)
+    assert all(r.status == 0 for r in recs_s), "served sparse fill failed"
+    busy = max(r.t_done for r in recs_s) - min(r.t_start for r in recs_s)
+    sat = n_sat * C * X * N * 2 / (busy * 1e-6) / 1e9
+    st = srv.stats()
+    srv.close()
+    del pool
+    torch.cuda.empty_cache()
+    peak = measured_peaks()[0]
+    out["served"] = {"workload": f"stream of sparse 24 x 54 x 560,000 fills (per-crystal noise sigma 3/sqrt(54)) from "
+                                 f"{n_pool} device-resident fills, DAQ_SPARSE; bursts of 8 fills 1 ms apart (10x)",
+                     "10x": {"fills": n, "latency_ms": {"p50": round(sm.latency_p50_us / 1e3, 4),
+                                                        "p99": round(sm.latency_p99_us / 1e3, 4)},
+                             "p99_under_fill_spacing": bool(sm.latency_p99_us < 1e3), "deadtime": round(sm.deadtime, 4),
+                             "served_gbs": round(sm.gbs, 2), "clocks": clk.summary()},
+                     "saturated": {"value": round(sat, 2), "unit": UNIT, "fills": n_sat,
+                                   "pct_of_hbm_peak": round(100.0 * sat / peak, 2), "max_running": st["max_running"]}}
+    out["batched"]["pct_of_hbm_peak"] = round(100.0 * out["batched"]["value"] / peak, 2)
+    return out
 
 
 def served_host_input(args, torch, dev, daq, params, C, X, N, dev_fills) -> dict:

@@ -597,7 +597,7 @@ class DaqServer:
 
     def __init__(self, n_calo: int, n_xtal: int, n_samples: int, budget_bytes: int, threshold=30, pre=8, post=24,
                  ped_samples=100, decim=(32,), tile=0, grid=0, max_slots=0, n_streams=0, hdr_cap=0, pool_cap=0,
-                 host_input=False, auto_release=False, device=None, q=None):
+                 host_input=False, auto_release=False, device=None, q=None, flags=0):
         import torch
         self.torch = torch
         dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
@@ -607,7 +607,7 @@ class DaqServer:
                                                      device=dev)
         cfg = DaqServerConfig()
         cfg.n_calo, cfg.n_xtal, cfg.n_samples = self.shape
-        cfg.params = make_params(threshold, pre, post, ped_samples, decim, 0, None, 0, tile, grid)
+        cfg.params = make_params(threshold, pre, post, ped_samples, decim, 0, None, flags, tile, grid)
         cfg.mem_budget_bytes = int(budget_bytes)
         cfg.max_slots, cfg.n_streams = int(max_slots), int(n_streams)
         cfg.hdr_cap, cfg.pool_row_cap = int(hdr_cap), int(pool_cap)

@@ -169,6 +169,34 @@ def test_each_fill_is_the_same_alone_and_in_the_mix(genv):
 
 
 @pytest.mark.gpu
+def test_sparse_fills_served_with_the_sparse_flag(genv):
+    """Processing flags reach the served fills: sparse fills served with
+    DAQ_SPARSE, several at once, each match the oracle."""
+    torch, daq, oracle = genv["torch"], genv["daq"], genv["oracle"]
+    from synth import workloads as W
+    w = W.scaled(W.SPARSE_FULL_FILL, n_fills=4, n_calo=2)
+    s = genv["synth"].generate(w.config())
+    F, C, X, N = s.shape
+    dev = [torch.from_numpy(s[f]).cuda() for f in range(F)]
+    srv = _server(genv, w, C, N, 1 << 40, max_slots=4, n_streams=4, flags=daq.DAQ_SPARSE)
+    tickets = [srv.submit(dev[f]) for f in range(F)]
+    q_ref = 0
+    for f, t in enumerate(tickets):
+        r = srv.wait(t)
+        assert r["status"] == daq.DAQ_OK
+        isl, pool, ped = srv.fetch(t)[:3]
+        srv.release(t)
+        ref = oracle.process_fills(s[f:f + 1], w.params(), n_threads=8)
+        isl = isl.copy()
+        isl["fill"] = 0
+        assert np.array_equal(isl, ref["islands"]) and np.array_equal(pool, ref["pool"]), f
+        assert np.array_equal(ped, ref["pedestal"][0]), f
+        q_ref = q_ref + ref["q"]
+    assert np.array_equal(srv.q.cpu().numpy(), q_ref)
+    srv.close()
+
+
+@pytest.mark.gpu
 def test_admission_respects_the_memory_budget(genv):
     torch, daq = genv["torch"], genv["daq"]
     w, s, fl = _fills(genv, 8)
