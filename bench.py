@@ -494,7 +494,9 @@ def bench_batched(args, torch, dev, daq, synth, W, w=None, plain_flags=0) -> dic
     q = torch.zeros(daq.q_size(C, N, params["decim"]), dtype=torch.int64, device=dev)
     fl_d = torch.as_tensor(np.asarray(fl, np.int32), device=dev)
     t1 = time.perf_counter()
-    plan = daq.BatchPlan(samples, q, out, fill_len=fl_d, tune=True, **params)
+    # tuned on this batch's own data (the library remembers a choice per shape and parameters, and
+    # the dense and sparse batches share both)
+    plan = daq.BatchPlan(samples, q, out, fill_len=fl_d, tune=True, force=True, **params)
     tune_s = time.perf_counter() - t1
     tuning = plan.tuning()
     stream = torch.cuda.Stream(dev)
