@@ -381,7 +381,10 @@ int daq_process_fills_static(const int16_t *samples, int n_calo, int n_xtal, int
  *                widths 128/224/384/448 with 2 or 1 CTAs per SM; the
  *                single-launch form at 448) on this batch and keep the
  *                fastest.  The choice is remembered per (device, sizes,
- *                windows, decimation, flags) for the rest of the process.
+ *                windows, decimation, flags) for the rest of the process,
+ *                whatever the data: a batch of the same shape whose islands
+ *                are much sparser or denser (DAQ_SPARSE wins on one and not
+ *                the other) should be tuned with DAQ_TUNE_FORCE.
  *                DAQ_TUNE_FORCE: ignore a remembered choice.
  *   *plan        receives the plan (NULL on error).
  * Creation is not the hot call: it may allocate, synchronises the device, and
