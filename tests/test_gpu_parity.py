@@ -129,14 +129,16 @@ def test_uneven_batch_of_fills(env):
     compare(env, s, w.params(), fill_len=fl)
 
 
-@pytest.mark.parametrize("tile,grid", [(0, 0), (384, 0), (448, 0), (0, -6)])
-def test_stress_parameters(env, tile, grid):
-    """post = 64: the default plan takes 384-sample tiles (two count CTAs per
-    SM); 448 runs one count CTA per SM with three tile slots."""
+@pytest.mark.parametrize("tile,grid,flags", [(0, 0, 0), (384, 0, 0), (448, 0, 0), (0, -6, 0), (0, 0, 32)])
+def test_stress_parameters(env, tile, grid, flags):
+    """post = 64: the default plan keeps 448-sample tiles with the halo-free
+    count pass (the scan completes each tile's marks); 384 is the halo'd plan;
+    flags 32 (DAQ_SPARSE) passes the halo-free records to the sparse compact
+    loop."""
     from synth import workloads as W
     w = W.scaled(W.STRESS, n_fills=2, n_calo=3)
     s = env["synth"].generate(w.config())
-    res, ref = compare(env, s, w.params(), tile=tile, grid=grid)
+    res, ref = compare(env, s, w.params(), tile=tile, grid=grid, flags=flags)
     assert ref["n_rows"] > 0.95 * s.shape[0] * s.shape[1] * s.shape[3]   # heavy merging
 
 
