@@ -94,6 +94,14 @@ __global__ void __launch_bounds__(kThreads) xtal_sum_kernel(const int16_t *sampl
         long long acc[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc[k] = 0;
+        long long *dst = q + row * pitch + t0;
+        const bool vec_q = kVec && t0 + 8 <= pitch;
+        longlong2 o[4];
+        if (vec_q) {  // the accumulators' loads go out before the samples'
+            const longlong2 *d2 = reinterpret_cast<const longlong2 *>(dst);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[k] = d2[k];
+        }
         for (int f = 0; f < n_fills; ++f) {
             const long long len = lens[f];
             if (t0 >= len) continue;
@@ -113,15 +121,13 @@ __global__ void __launch_bounds__(kThreads) xtal_sum_kernel(const int16_t *sampl
                     if (t0 + k < len) acc[k] += (long long)src[k] - P;
             }
         }
-        long long *dst = q + row * pitch + t0;
-        if (kVec && t0 + 8 <= pitch) {
+        if (vec_q) {
             longlong2 *d2 = reinterpret_cast<longlong2 *>(dst);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                longlong2 o = d2[k];
-                o.x += acc[2 * k];
-                o.y += acc[2 * k + 1];
-                d2[k] = o;
+                o[k].x += acc[2 * k];
+                o[k].y += acc[2 * k + 1];
+                __stcs(d2 + k, o[k]);
             }
         } else {
 #pragma unroll
